@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Throughput of the batched CFG-pair similarity on one GB300 (or N, one rank each).
+
+Workload: all 19,900 pairs of 200 seeded synthetic CFGs (block counts
+log-uniform in 8..120, structured sequence / diamond / loop grammar, 12
+instruction-category counts + registers per block, Dirichlet branch
+probabilities), K = 40, alpha = 0.8.  One step = the whole forward hot path
+over the batch: device-side plan (cost order, offsets), the persistent
+iteration kernel (attribute term, 40 renormalised iterations, greedy
+matching, graph score) -- through the C ABI.
+
+Output: one JSON line on rank 0 (see the keys below).  ``--impl reference``
+times the FP64 CPU oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")  # the CPU oracle runs single-threaded (cores = 1)
+
+import argparse  # noqa: E402
+import hashlib  # noqa: E402
+import json  # noqa: E402
+import re  # noqa: E402
+import statistics  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import threading  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CFG-pair similarity evals/sec (fwd, fwd+bwd) batched vs per-pair, % roofline"
+UNIT = "pairs/s"
+ALPHA, K_ITERS = 0.8, 40
+WORKLOAD = ("cfg2: all 19,900 pairs of 200 seeded CFGs, n log-uniform 8-120, depth<=5, F=13 "
+            "(12 instruction categories + registers), K=40, alpha=0.8, greedy matching + score")
+
+
+def workload():
+    from gen import config2
+
+    return config2()
+
+
+def algorithmic(w, K):
+    """Per-launch algorithmic counts of the iteration kernel.
+
+    On-chip bytes: every iteration reads each gathered neighbour-pair entry
+    once (e_a * e_b successor pairs + e_a * e_b predecessor pairs), reads
+    (1 - alpha) Ehat once and writes Y once per entry, 4 bytes each.
+    HBM bytes: the pack (read once), the pair list, scores and matchings.
+    FLOPs: attribute term n_a n_b (2F + 3) plus per iteration 4 per gathered
+    pair and 5 per entry."""
+    n = np.array([c.n for c in w.cfgs_a], np.int64)
+    e = np.array([len(set(zip(c.src.tolist(), c.dst.tolist()))) for c in w.cfgs_a], np.int64)
+    a, b = w.pairs[:, 0], w.pairs[:, 1]
+    nn = n[a] * n[b]
+    ee = e[a] * e[b]
+    onchip = int((K * 4 * (2 * ee + 2 * nn)).sum())
+    flops = int((nn * (2 * w.F + 3) + K * (4 * ee + 5 * nn)).sum())
+    return onchip, flops, int(nn.sum()), int(n[a].sum())
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            self.proc.wait(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if len(r) > 5 + k and r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def profiled_traffic(kernel_src: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    with the current kernel source (sha256 of forward.cu); else None."""
+    path = os.path.join(ROOT, "profiles", "fwd_batched_kernel_cfg2.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", txt)
+    h = re.search(r"forward_cu_sha256:\s*([0-9a-f]{64})", txt)
+    cur = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    if m and h and h.group(1) == cur:
+        return int(m.group(1))
+    return None
+
+
+def cpu_oracle(w, seconds: float, seed: int = 0):
+    """The FP64 oracle as it stands, single-threaded, on a seeded random
+    sample of the workload's pairs, until `seconds` have elapsed."""
+    import oracle
+
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(len(w.pairs))
+    om = np.ones(w.F)
+    t0 = time.perf_counter()
+    done = 0
+    for p in order:
+        a, b = w.pairs[p]
+        oracle.pair_score(w.cfgs_a[a], w.cfgs_b[b], om, ALPHA, K_ITERS)
+        done += 1
+        if time.perf_counter() - t0 >= seconds and done >= 20:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt
+
+
+def dist_setup(n_gpus):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle, timed on the host cores."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload()
+    import oracle
+
+    om = np.ones(w.F)
+    rng = np.random.default_rng(1)
+    order = rng.permutation(len(w.pairs))
+    # size each step so that warmup + steps take about 90 s on this host
+    t0 = time.perf_counter()
+    for p in order[:10]:
+        a, b = w.pairs[p]
+        oracle.pair_score(w.cfgs_a[a], w.cfgs_b[b], om, ALPHA, K_ITERS)
+    t_pair = (time.perf_counter() - t0) / 10
+    per_step = int(min(300, max(3, 90.0 / ((args.steps + args.warmup) * t_pair))))
+    sample = order[:per_step]
+
+    def step():
+        for p in sample:
+            a, b = w.pairs[p]
+            oracle.pair_score(w.cfgs_a[a], w.cfgs_b[b], om, ALPHA, K_ITERS)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    v = len(sample) * args.steps / dt
+    desc = f"{per_step} seeded random pairs of the workload per step, single-threaded FP64 oracle (numpy/scipy)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "reference": "FP64 CPU oracle (oracle/isorank.py), host cores"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ours(args):
+    import ctypes as C
+
+    import torch
+
+    from paper_1707_02423_gb300 import _binding as B
+    from paper_1707_02423_gb300 import api
+
+    world, rank, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w = workload()
+    P = len(w.pairs)
+    pairs_np = np.ascontiguousarray(w.pairs, np.int32)
+    pack = api.Pack(w.cfgs_a, w.F, device=dev)
+    omega = torch.ones(w.F, dtype=torch.float32, device=dev)
+    d_pairs = torch.from_numpy(pairs_np).to(dev)
+    ws = api.Workspace(dev)
+    prm = B.params(ALPHA, K_ITERS)
+    ws_bytes = api.ws_size(pack, pack, pairs_np, prm)
+    x_off, m_off = api.out_offsets(pack, pack, pairs_np)
+    out = {"scores": torch.empty(P, dtype=torch.float32, device=dev),
+           "match": torch.empty(int(m_off[-1]), dtype=torch.int32, device=dev)}
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def sim(flags):
+        api.similarity(pack, pack, pairs_np, omega, ALPHA, K_ITERS, want_match=True, ws=ws, d_pairs=d_pairs,
+                       out=out, check_status=False, flags=flags, ws_bytes=ws_bytes)
+
+    def step():
+        sim(B.CF_FLAG_PLAN_ONLY)
+        sim(B.CF_FLAG_REUSE_PLAN)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    B.check(B.lib().cf_status_check(ws.get(ws_bytes).data_ptr(), int(stream.cuda_stream)))
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()  # outside the step's events
+            ev[i][0].record(stream)
+            sim(B.CF_FLAG_PLAN_ONLY)
+            ev[i][1].record(stream)
+            sim(B.CF_FLAG_REUSE_PLAN)
+            ev[i][2].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    step_ms = [e[0].elapsed_time(e[2]) for e in ev]
+    fwd_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    tot_ms = float(sum(step_ms))
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([tot_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+        dist.barrier()
+    B.check(B.lib().cf_status_check(ws.get(ws_bytes).data_ptr(), int(stream.cuda_stream)))
+    ms_per_step = tot_ms / args.steps
+    value = world * P / (ms_per_step * 1e-3)
+
+    # ---- per-pair form: one launch per pair, same math
+    pp_steps = 2
+    for _ in range(1):
+        api.similarity(pack, pack, pairs_np, omega, ALPHA, K_ITERS, want_match=True, ws=ws, d_pairs=d_pairs,
+                       out=out, check_status=False, per_pair=True, ws_bytes=ws_bytes)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(pp_steps):
+        flush.zero_()
+        api.similarity(pack, pack, pairs_np, omega, ALPHA, K_ITERS, want_match=True, ws=ws, d_pairs=d_pairs,
+                       out=out, check_status=False, per_pair=True, ws_bytes=ws_bytes)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pp_ms = e0.elapsed_time(e1) / pp_steps
+
+    # ---- end to end through the C ABI with host buffers: build + upload the
+    # pack from the host CFG arrays, upload the pairs from pinned memory,
+    # compute, read scores and matchings back into pinned memory
+    L = B.lib()
+    pairs_pin = torch.from_numpy(pairs_np).pin_memory()
+    sc_pin = torch.empty(P, dtype=torch.float32).pin_memory()
+    mt_pin = torch.empty(int(m_off[-1]), dtype=torch.int32).pin_memory()
+    dpack = torch.empty(pack.host.size, dtype=torch.uint8, device=dev)
+    wbuf = ws.get(ws_bytes)
+    e2e_steps = max(3, min(20, args.steps // 10))
+    e2e_ts = []
+    for it in range(e2e_steps + 2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.check(L.cf_pack_cfgs(pack._views, pack.n_cfgs, w.F, dpack.data_ptr(), dpack.numel(),
+                               int(stream.cuda_stream)))
+        d_pairs.copy_(pairs_pin, non_blocking=True)
+        B.check(L.cf_similarity(dpack.data_ptr(), dpack.data_ptr(), d_pairs.data_ptr(), P, C.byref(prm),
+                                omega.data_ptr(), None, out["scores"].data_ptr(), out["match"].data_ptr(),
+                                wbuf.data_ptr(), ws_bytes, int(stream.cuda_stream)))
+        sc_pin.copy_(out["scores"], non_blocking=True)
+        mt_pin.copy_(out["match"], non_blocking=True)
+        torch.cuda.synchronize()
+        if it >= 2:
+            e2e_ts.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(e2e_ts)
+    h2d = int(pack.host.size + pairs_np.nbytes)
+    d2h = int(sc_pin.numel() * 4 + mt_pin.numel() * 4)
+
+    if rank != 0:
+        return
+    onchip, flops, x_elems, m_elems = algorithmic(w, K_ITERS)
+    fwd_mean_s = statistics.mean(fwd_ms) * 1e-3
+    clk = clk.summary()
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    f_mhz = clk["sm_mhz"] or measured_peaks().get("clocks_under_load", {}).get("sm_mhz_median", 1432.0)
+    smem_peak_gbs = 128.0 * n_sm * f_mhz * 1e6 / 1e9  # 128 B/clk/SM shared-memory bandwidth
+    achieved = onchip / fwd_mean_s / 1e9
+    peaks = measured_peaks()
+    hbm_bytes = int(pack.host.size + pairs_np.nbytes + P * 4 + m_elems * 4)
+    traffic = profiled_traffic(os.path.join(ROOT, "paper_1707_02423_gb300", "csrc", "forward.cu"))
+    cpu_v, cpu_n, cpu_dt = cpu_oracle(w, args.cpu_seconds)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "pairs": P, "n_cfgs": len(w.cfgs_a), "F": w.F, "K": K_ITERS,
+                   "alpha": ALPHA, "l2": "flushed between steps (256 MiB write, outside the step events)",
+                   "step": "plan kernels + persistent forward kernel (sum of per-step CUDA events)"},
+        "roofline": {"bound": "smem", "kernel": "fwd_batched_kernel", "achieved": achieved,
+                     "peak": smem_peak_gbs, "unit": "GB/s", "frac": achieved / smem_peak_gbs,
+                     "traffic": traffic,
+                     "peak_source": f"derived: 128 B/clk/SM x {n_sm} SMs x {f_mhz:.0f} MHz (median SM clock sampled)",
+                     "algorithmic_bytes_per_launch": onchip, "kernel_ms": fwd_mean_s * 1e3,
+                     "flops_per_launch": flops, "achieved_tflops_fp32": flops / fwd_mean_s / 1e12,
+                     "hbm": {"algorithmic_bytes_per_step": hbm_bytes,
+                             "achieved_gbs": hbm_bytes / (ms_per_step * 1e-3) / 1e9,
+                             "peak_gbs": peaks.get("hbm_gbs"),
+                             "frac": (hbm_bytes / (ms_per_step * 1e-3) / 1e9) / peaks["hbm_gbs"]
+                             if peaks.get("hbm_gbs") else None, "peak_source": "MEASURED_PEAKS.json (of measured)"}},
+        "per_pair": {"value": P / (pp_ms * 1e-3), "unit": UNIT, "ms_per_step": pp_ms, "launches_per_step": P,
+                     "speedup_batched_over_per_pair": pp_ms / ms_per_step},
+        "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{cpu_n} seeded random pairs of the workload in {cpu_dt:.1f} s, "
+                                   "single-threaded FP64 oracle (numpy/scipy)"},
+        "e2e": {"value": world * P / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_s * 1e3,
+                "what": "cf_pack_cfgs (host build + copy) + pinned pair upload + cf_similarity + pinned "
+                        "readback of scores and matchings, wall clock"},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clk,
+        "wall_s_timed_region": t_wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+"""Python API over the C ABI: packs, workspaces, and the similarity calls.
+
+PyTorch supplies device memory and streams only; every step of the path runs
+in libcfsim.so's kernels.  Tensors passed in must live on the current CUDA
+device.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _binding as B
+
+
+def _stream_ptr(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else int(t.data_ptr())
+
+
+class Pack:
+    """A CSR batch pack of CFGs (include/cfsim.h, "a1").
+
+    ``cfgs`` is a sequence of objects with ``n``, ``src``, ``dst``, ``w`` and
+    ``attr`` ([n, F]).  Keeps the host bytes (for sizing queries) and a device
+    copy made by ``cf_pack_cfgs``."""
+
+    def __init__(self, cfgs, F: int, device="cuda"):
+        L = B.lib()
+        self.F = int(F)
+        self.n_blocks = np.array([int(c.n) for c in cfgs], dtype=np.int64)
+        self.n_user_edges = np.array([int(len(c.src)) for c in cfgs], dtype=np.int64)
+        keep = []
+        views = (B.cf_cfg_view * len(cfgs))()
+        for k, c in enumerate(cfgs):
+            src = np.ascontiguousarray(c.src, dtype=np.int32)
+            dst = np.ascontiguousarray(c.dst, dtype=np.int32)
+            w = np.ascontiguousarray(c.w, dtype=np.float32)
+            attr = np.ascontiguousarray(c.attr, dtype=np.float32)
+            if attr.shape != (int(c.n), self.F):
+                raise ValueError(f"cfg {k}: attr shape {attr.shape} != ({c.n}, {self.F})")
+            keep += [src, dst, w, attr]
+            views[k] = B.cf_cfg_view(int(c.n), int(src.size), src.ctypes.data, dst.ctypes.data, w.ctypes.data,
+                                     attr.ctypes.data)
+        self._views, self._keep = views, keep
+        nbytes = C.c_size_t(0)
+        B.check(L.cf_pack_size(views, len(cfgs), self.F, C.byref(nbytes)))
+        self.host = np.zeros(nbytes.value, dtype=np.uint8)
+        B.check(L.cf_pack_host(views, len(cfgs), self.F, self.host.ctypes.data, nbytes.value))
+        info = B.cf_pack_info()
+        B.check(L.cf_pack_info_get(self.host.ctypes.data, C.byref(info)))
+        self.info = info
+        self.n_cfgs = info.n_cfgs
+        self.dev = None
+        if device is not None:
+            self.dev = torch.empty(nbytes.value, dtype=torch.uint8, device=device)
+            B.check(L.cf_pack_cfgs(views, len(cfgs), self.F, self.dev.data_ptr(), nbytes.value,
+                                   _stream_ptr(None)))
+        self._keep = None  # the host pack is self-contained
+
+    @property
+    def host_ptr(self) -> int:
+        return self.host.ctypes.data
+
+    def set_weights(self, w_user: torch.Tensor, stream=None) -> None:
+        """Replace the edge weights (user edge order, float32 on the device)."""
+        w = w_user.detach().to(torch.float32).contiguous()
+        if w.numel() != int(self.info.n_user_edges):
+            raise ValueError("w_user has the wrong length")
+        B.check(B.lib().cf_pack_set_weights(self.dev.data_ptr(), self.host_ptr, w.data_ptr(), _stream_ptr(stream)))
+
+
+def out_offsets(pa: Pack, pb: Pack, pairs: np.ndarray):
+    """Host copies of x_off and m_off (length P + 1) for a pair list."""
+    pairs = np.asarray(pairs, dtype=np.int64)
+    na = pa.n_blocks[pairs[:, 0]]
+    nb = pb.n_blocks[pairs[:, 1]]
+    x_off = np.concatenate([[0], np.cumsum(na * nb)])
+    m_off = np.concatenate([[0], np.cumsum(na)])
+    return x_off, m_off
+
+
+class Workspace:
+    """A reusable device workspace; grows to the largest size asked for."""
+
+    def __init__(self, device="cuda"):
+        self.device = device
+        self.buf = None
+
+    def get(self, nbytes: int) -> torch.Tensor:
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=self.device)
+        return self.buf
+
+
+@dataclass
+class Result:
+    scores: torch.Tensor | None
+    match: torch.Tensor | None
+    X: torch.Tensor | None
+    x_off: np.ndarray
+    m_off: np.ndarray
+
+    def X_of(self, p: int, na: int, nb: int) -> torch.Tensor:
+        return self.X[int(self.x_off[p]):int(self.x_off[p + 1])].view(na, nb)
+
+
+def _pairs_np(pairs) -> np.ndarray:
+    p = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    return p
+
+
+def ws_size(pa: Pack, pb: Pack, pairs_np: np.ndarray, prm: B.cf_params) -> int:
+    n = C.c_size_t(0)
+    B.check(B.lib().cf_similarity_ws_size(pa.host_ptr, pb.host_ptr, pairs_np.ctypes.data, len(pairs_np),
+                                          C.byref(prm), C.byref(n)))
+    return n.value
+
+
+def similarity(pa: Pack, pb: Pack, pairs, omega: torch.Tensor, alpha: float = 0.8, K: int = 40, *,
+               want_x: bool = False, want_scores: bool = True, want_match: bool = False, per_pair: bool = False,
+               norm_mode: int = B.CF_NORM_FROB, ws: Workspace | None = None, d_pairs: torch.Tensor | None = None,
+               out: dict | None = None, stream=None, check_status: bool = True, flags: int = 0,
+               ws_bytes: int | None = None) -> Result:
+    """X_K, graph scores and greedy matchings for every pair (cf_similarity).
+
+    ``pairs``: int [P, 2] host array of (CFG of pa, CFG of pb).  ``omega``: float32
+    [F] on the device.  ``out`` may hold preallocated ``scores`` / ``match`` /
+    ``X`` tensors (reused across calls, e.g. under CUDA-graph capture)."""
+    L = B.lib()
+    pairs_np = _pairs_np(pairs)
+    P = len(pairs_np)
+    dev = pa.dev.device
+    prm = B.params(alpha, K, norm_mode, (B.CF_FLAG_PER_PAIR_LAUNCH if per_pair else 0) | flags)
+    x_off, m_off = out_offsets(pa, pb, pairs_np)
+    out = {} if out is None else out
+    scores = out.get("scores") if want_scores else None
+    if want_scores and scores is None:
+        scores = torch.empty(P, dtype=torch.float32, device=dev)
+    match = out.get("match") if want_match else None
+    if want_match and match is None:
+        match = torch.empty(int(m_off[-1]), dtype=torch.int32, device=dev)
+    X = out.get("X") if want_x else None
+    if want_x and X is None:
+        X = torch.empty(int(x_off[-1]), dtype=torch.float32, device=dev)
+    if d_pairs is None:
+        d_pairs = torch.from_numpy(pairs_np).to(dev)
+    ws = ws or Workspace(dev)
+    nbytes = ws_size(pa, pb, pairs_np, prm) if ws_bytes is None else ws_bytes
+    wbuf = ws.get(nbytes)
+    omega = omega.contiguous()
+    st = _stream_ptr(stream)
+    B.check(L.cf_similarity(pa.dev.data_ptr(), pb.dev.data_ptr(), d_pairs.data_ptr(), P, C.byref(prm),
+                            omega.data_ptr(), _ptr(X), _ptr(scores), _ptr(match), wbuf.data_ptr(), wbuf.numel(), st))
+    if check_status:
+        B.check(L.cf_status_check(wbuf.data_ptr(), st))
+    return Result(scores, match, X, x_off, m_off)
+
+
+def match(pa: Pack, pb: Pack, pairs, X: torch.Tensor, *, ws: Workspace | None = None, stream=None) -> Result:
+    """Greedy matching and scores of caller-given matrices (cf_match with X)."""
+    L = B.lib()
+    pairs_np = _pairs_np(pairs)
+    P = len(pairs_np)
+    dev = pa.dev.device
+    x_off, m_off = out_offsets(pa, pb, pairs_np)
+    scores = torch.empty(P, dtype=torch.float32, device=dev)
+    mt = torch.empty(int(m_off[-1]), dtype=torch.int32, device=dev)
+    d_pairs = torch.from_numpy(pairs_np).to(dev)
+    ws = ws or Workspace(dev)
+    prm = B.params()
+    wbuf = ws.get(ws_size(pa, pb, pairs_np, prm))
+    X = X.contiguous()
+    st = _stream_ptr(stream)
+    B.check(L.cf_match(pa.dev.data_ptr(), pb.dev.data_ptr(), d_pairs.data_ptr(), P, None, None, X.data_ptr(),
+                       mt.data_ptr(), scores.data_ptr(), wbuf.data_ptr(), wbuf.numel(), st))
+    B.check(L.cf_status_check(wbuf.data_ptr(), st))
+    return Result(scores, mt, X, x_off, m_off)
+
+
+def topk(scores: torch.Tensor, k: int, stream=None):
+    """Per-row top-k of a [Q, C] float32 score matrix: (values, column indices)."""
+    s = scores.contiguous()
+    Q, Cn = s.shape
+    top = torch.empty(Q, k, dtype=torch.float32, device=s.device)
+    idx = torch.empty(Q, k, dtype=torch.int32, device=s.device)
+    B.check(B.lib().cf_topk(s.data_ptr(), Q, Cn, k, top.data_ptr(), idx.data_ptr(), _stream_ptr(stream)))
+    return top, idx

@@ -1,0 +1,62 @@
+// Host-side launchers of the kernels (implemented in the .cu files), called by
+// the C-ABI layer.  All launches are asynchronous on the given stream and make
+// no allocation.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "layout.h"
+
+namespace cfsim {
+
+// Arguments of one similarity / matching / backward call.
+struct CallArgs {
+  const void* pack_a;
+  const void* pack_b;
+  const int32_t* pairs;
+  int P;
+  float alpha;
+  int K;
+  int norm_mode;
+  const float* omega;
+  float* X;        // optional output
+  float* scores;   // optional output
+  int32_t* match;  // optional output
+  const float* X_in;  // cf_match on given matrices
+  unsigned char* ws;
+  size_t ws_bytes;
+  // backward
+  const int32_t* match_in;
+  const float* grad_scores;
+  float* grad_w_a;
+  float* grad_w_b;
+  float* grad_omega;
+};
+
+// Batched forward kernel variants (threads per CTA, rows per thread).
+struct FwdVariant {
+  int nt, reserved, min_blocks;
+  ClassCfg cc;
+};
+int num_fwd_variants();
+FwdVariant fwd_variant(int v);
+
+// a7: device-side plan: validate pairs, classify, cost-order them into the
+// queue, and compute the X / match offsets.
+cudaError_t launch_plan(const CallArgs& a, const ClassCfg& cc, cudaStream_t s);
+
+// a2-a6: the batched persistent forward (or one launch per pair).
+cudaError_t launch_forward(const CallArgs& a, int variant, bool per_pair, cudaStream_t s);
+
+// Greedy matching + score on caller-given matrices.
+cudaError_t launch_match_only(const CallArgs& a, cudaStream_t s);
+
+// Pack weight update from user-order weights (pointers into a device pack).
+cudaError_t launch_set_weights(CfAdj* out_adj, CfAdj* in_adj, const int32_t* in_eid, const int32_t* u2c,
+                               int64_t n_user_edges, int64_t n_edges, const float* w_user, cudaStream_t s);
+
+// Top-k per row.
+cudaError_t launch_topk(const float* scores, int Q, int C, int k, float* top, int32_t* idx, cudaStream_t s);
+
+
+}  // namespace cfsim

@@ -1,0 +1,173 @@
+// Byte layouts shared by the host runtime and the kernels: the CSR batch pack,
+// the workspace header, and the classification of a pair into an execution
+// class (warp-, CTA- or global-memory-resident).  Plain C++ so that host-only
+// translation units can include it.
+#pragma once
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __CUDACC__
+#define CF_HD __host__ __device__ __forceinline__
+#else
+#define CF_HD inline
+#endif
+
+namespace cfsim {
+
+constexpr uint32_t kPackMagic = 0x4B504643u;  // "CFPK"
+constexpr uint32_t kPackVersion = 1;
+constexpr int kMaxBlocks = 32000;  // per CFG; matching state packs indices in int16
+constexpr int kMaxF = 32;          // attributes per block
+constexpr size_t kAlign = 256;
+
+CF_HD size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+CF_HD int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// One adjacency entry: local index of the neighbour block and the edge weight.
+struct CfAdj {
+  int32_t nbr;
+  float w;
+};
+
+// Header at byte 0 of a pack.  Every offset is in bytes from the pack base.
+struct PackHeader {
+  uint32_t magic, version;
+  int32_t n_cfgs, F, F_pad, max_blocks;
+  int32_t max_out_deg, max_in_deg;
+  int64_t n_blocks, n_edges, n_user_edges, total_bytes;
+  int64_t off_node;   // int32 [n_cfgs + 1]  first block of each CFG
+  int64_t off_edge;   // int32 [n_cfgs + 1]  first distinct edge of each CFG
+  int64_t off_uedge;  // int32 [n_cfgs + 1]  first user edge of each CFG
+  int64_t off_out_ptr;  // int32 [n_blocks + 1] global index into out_adj per block
+  int64_t off_in_ptr;   // int32 [n_blocks + 1] global index into in_adj per block
+  int64_t off_out_adj;  // CfAdj [n_edges] sorted by (src, dst); position = distinct-edge id
+  int64_t off_in_adj;   // CfAdj [n_edges] sorted by (dst, src)
+  int64_t off_in_eid;   // int32 [n_edges] distinct-edge id of each in_adj entry
+  int64_t off_u2c;      // int32 [n_user_edges] distinct-edge id of each user edge
+  int64_t off_attr;     // float [n_blocks * F_pad]
+};
+
+// Execution classes of a pair, in queue order (largest work first).
+enum PairClass : int { kClassGlobal = 0, kClassCta = 1, kClassWarp = 2, kNumClasses = 3, kClassSkip = 3 };
+constexpr int kBuckets = 64;  // cost buckets per class (two per octave)
+
+// Tunable shape of the batched forward kernel.  The plan and the kernel
+// classify pairs with the same values.
+struct ClassCfg {
+  int nt;         // threads per CTA
+  int ccap;       // floats per resident buffer of a CTA-class pair (n_row * ld)
+  int wcap;       // floats per resident buffer of a warp-class pair
+  int warp_rows;  // max rows of a warp-class pair (bounds the matching state)
+  int cta_rows;   // max rows of a CTA-class pair
+};
+
+// How a pair maps onto a group of G threads.  The "row" graph indexes the
+// rows of the resident matrix, the "column" graph its columns; tr = 1 when
+// the row graph is B (the matrix is then X^T).  Thread g < R * n_col owns
+// column g % n_col and rows g / n_col + R * m, m < M.
+struct Shape {
+  int cls, tr, n_row, n_col, R, M, ld;
+};
+
+CF_HD int pair_ld(int n_col) { return n_col | 1; }  // odd stride: column scans hit distinct banks
+
+CF_HD bool fits(int n_row, int n_col, int G, int rows_cap, int cap, int* R, int* M) {
+  if (n_col > G || n_row > rows_cap) return false;
+  *R = G / n_col;
+  *M = ceil_div(n_row, *R);
+  return (int64_t)n_row * pair_ld(n_col) <= cap;
+}
+
+// Smallest class that holds the pair, and the orientation with the fewest
+// rows per thread (ties: untransposed).
+CF_HD Shape classify(int na, int nb, const ClassCfg& c) {
+  Shape s{};
+  for (int cls = kClassWarp; cls >= kClassCta; --cls) {
+    int G = cls == kClassWarp ? 32 : c.nt;
+    int rows_cap = cls == kClassWarp ? c.warp_rows : c.cta_rows;
+    int cap = cls == kClassWarp ? c.wcap : c.ccap;
+    int R0 = 0, M0 = 0, R1 = 0, M1 = 0;
+    bool f0 = fits(na, nb, G, rows_cap, cap, &R0, &M0);
+    bool f1 = fits(nb, na, G, rows_cap, cap, &R1, &M1);
+    if (f0 || f1) {
+      bool tr = !f0 || (f1 && M1 < M0);
+      s.cls = cls;
+      s.tr = tr ? 1 : 0;
+      s.n_row = tr ? nb : na;
+      s.n_col = tr ? na : nb;
+      s.R = tr ? R1 : R0;
+      s.M = tr ? M1 : M0;
+      s.ld = pair_ld(s.n_col);
+      return s;
+    }
+  }
+  s.cls = kClassGlobal;
+  s.tr = 0;
+  s.n_row = na;
+  s.n_col = nb;
+  s.R = 0;
+  s.M = 0;
+  s.ld = nb;
+  return s;
+}
+
+// Scratch a global-class pair needs: three n_a x n_b float matrices (two
+// iterates and Ehat), row/column norms and the int32 matching state.
+CF_HD size_t global_slot_bytes(int na, int nb) {
+  size_t e = (size_t)na * nb;
+  return align_up(4 * (3 * e + 2 * (size_t)(na + nb) + 2 * (size_t)na + nb + 64), kAlign);
+}
+
+// Cost bucket: two buckets per octave of the per-iteration work.
+CF_HD int cost_bucket(int64_t cost) {
+  int b = 0;
+  uint64_t v = (uint64_t)(cost > 0 ? cost : 1);
+  while (v >= 4 && b < kBuckets - 2) {  // b ~ 2 log2(cost) capped
+    v >>= 1;
+    b += 2;
+  }
+  if (v >= 3 && b < kBuckets - 1) b += 1;
+  return b;
+}
+
+// Workspace header (first bytes of the workspace, zeroed at every call).
+struct WsHeader {
+  int32_t status;       // first device-side error (cf_status code), 0 = none
+  int32_t status_info;  // pair index or other detail of that error
+  uint32_t q_next[kNumClasses];
+  uint32_t n_class[kNumClasses];
+  uint64_t slot_need;  // bytes of scratch the largest global-class pair needs
+  uint32_t hist[kNumClasses][kBuckets];
+  uint32_t cursor[kNumClasses][kBuckets];
+  int64_t x_total, m_total;
+};
+
+// Byte offsets of the forward workspace sections for P pairs.
+struct WsLayout {
+  size_t hdr, queue, x_off, m_off, bsum, scratch, fixed_bytes;
+  int plan_blocks;
+};
+
+constexpr int kPlanThreads = 256;
+
+CF_HD WsLayout ws_layout(int P) {
+  WsLayout L{};
+  size_t o = 0;
+  L.hdr = o;
+  o = align_up(o + sizeof(WsHeader), kAlign);
+  L.queue = o;
+  o = align_up(o + 4 * (size_t)(P > 0 ? P : 1), kAlign);
+  L.x_off = o;
+  o = align_up(o + 8 * (size_t)(P + 1), kAlign);
+  L.m_off = o;
+  o = align_up(o + 8 * (size_t)(P + 1), kAlign);
+  L.plan_blocks = ceil_div(P > 0 ? P : 1, kPlanThreads);
+  L.bsum = o;
+  o = align_up(o + 2 * 8 * (size_t)L.plan_blocks, kAlign);
+  L.scratch = o;
+  L.fixed_bytes = o;
+  return L;
+}
+
+}  // namespace cfsim
