@@ -206,6 +206,30 @@ cf_status cf_similarity_backward(const void* d_pack_a, const void* d_pack_b, con
 cf_status cf_topk(const float* d_scores, int32_t Q, int32_t C, int32_t k, float* d_top, int32_t* d_idx,
                   cf_stream_t stream);
 
+/* ---- no-allocation variant ------------------------------------------------- */
+/* cf_similarity without a workspace argument, for callers that cannot
+ * allocate device memory (code running under an allocator that owns the whole
+ * device heap, inside host callbacks, or in a serving loop that must not add
+ * allocation latency).  The paper has no counterpart; this is a library
+ * convenience.  The workspace is a file-scope 32 MiB device array that every
+ * GPU loading the library holds until exit; nothing is allocated per call.
+ * Same arguments and outputs as cf_similarity, plus d_status: when not NULL,
+ * one int32 on the device that receives this call's device status word
+ * (a cf_status code) in stream order.
+ *   - A pair list whose fixed workspace part (about 20 bytes per pair) does
+ *     not fit in 32 MiB is rejected with CF_ERR_WORKSPACE before any launch;
+ *     pairs too large for shared memory need scratch slots from the rest of
+ *     the array, and *d_status is CF_ERR_WORKSPACE if none fits.
+ *   - All calls share the array; each call clears what must start at zero.
+ *     Calls whose device work can overlap (other streams without ordering)
+ *     race on the array and give wrong results.
+ *   - The first call on a device resolves the array's address
+ *     (cudaGetSymbolAddress, that device current): make it before any stream
+ *     capture begins. */
+cf_status cf_similarity_noalloc(const void* d_pack_a, const void* d_pack_b, const int32_t* d_pairs, int32_t P,
+                                const cf_params* params, const float* d_omega, float* d_X, float* d_scores,
+                                int32_t* d_match, int32_t* d_status, cf_stream_t stream);
+
 /* ---- status word ---------------------------------------------------------- */
 /* Read the device status word of the last call that used d_ws.  BLOCKS
  * (synchronises `stream`).  Returns CF_OK or the first device-side error. */

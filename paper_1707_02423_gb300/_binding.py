@@ -57,6 +57,7 @@ SIGNATURES = {
     "cf_similarity_backward": (_i32, [_p, _p, _p, _i32, C.POINTER(cf_params), _p, _p, _p, _p, _p, _p, _p,
                                       C.c_size_t, _p]),
     "cf_topk": (_i32, [_p, _i32, _i32, _i32, _p, _p, _p]),
+    "cf_similarity_noalloc": (_i32, [_p, _p, _p, _i32, C.POINTER(cf_params), _p, _p, _p, _p, _p, _p]),
     "cf_status_check": (_i32, [_p, _p]),
 }
 

@@ -310,6 +310,11 @@ cf_status check_device_call(const void* d_pack_a, const void* d_pack_b, const in
 
 }  // namespace
 
+namespace cfsim {
+// Set the calling thread's error detail from another translation unit.
+void set_error_detail(const char* msg) { g_err = msg ? msg : ""; }
+}  // namespace cfsim
+
 extern "C" {
 
 const char* cf_status_string(cf_status s) {
