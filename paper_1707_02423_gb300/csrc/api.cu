@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstddef>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -257,6 +258,8 @@ cf_status scan_pairs(const void* h_pack_a, const void* h_pack_b, const int32_t* 
   if (P > 0 && !h_pairs) return fail(CF_ERR_INVALID_ARG, "h_pairs is NULL");
   const int32_t* noa = reinterpret_cast<const int32_t*>(static_cast<const char*>(h_pack_a) + ha.off_node);
   const int32_t* nob = reinterpret_cast<const int32_t*>(static_cast<const char*>(h_pack_b) + hb.off_node);
+  const int32_t* eoa = reinterpret_cast<const int32_t*>(static_cast<const char*>(h_pack_a) + ha.off_edge);
+  const int32_t* eob = reinterpret_cast<const int32_t*>(static_cast<const char*>(h_pack_b) + hb.off_edge);
   int64_t xs = 0, ms = 0, ng = 0;
   size_t need = 0;
   const ClassCfg cc = fwd_variant(0).cc;
@@ -267,7 +270,7 @@ cf_status scan_pairs(const void* h_pack_a, const void* h_pack_b, const int32_t* 
     const int na = noa[a + 1] - noa[a], nb = nob[b + 1] - nob[b];
     xs += (int64_t)na * nb;
     ms += na;
-    if (classify(na, nb, cc).cls == kClassGlobal) {
+    if (classify(na, nb, eoa[a + 1] - eoa[a], eob[b + 1] - eob[b], cc).cls == kClassGlobal) {
       need = std::max(need, global_slot_bytes(na, nb));
       ++ng;
     }
@@ -277,6 +280,16 @@ cf_status scan_pairs(const void* h_pack_a, const void* h_pack_b, const int32_t* 
   if (slot_need) *slot_need = need;
   if (n_global) *n_global = ng;
   return CF_OK;
+}
+
+// Forward kernel variant: CFSIM_FWD_VARIANT overrides the default (0).
+int active_variant() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("CFSIM_FWD_VARIANT");
+    v = (e && *e >= '0' && *e < '0' + num_fwd_variants()) ? *e - '0' : 0;
+  }
+  return v;
 }
 
 CallArgs base_args(const void* d_pack_a, const void* d_pack_b, const int32_t* d_pairs, int32_t P,
@@ -439,11 +452,11 @@ cf_status cf_similarity(const void* d_pack_a, const void* d_pack_b, const int32_
   } else {
     e = cudaMemsetAsync(d_ws, 0, sizeof(WsHeader), st);
     if (e != cudaSuccess) return cuda_fail(e, "workspace reset");
-    e = launch_plan(a, fwd_variant(0).cc, st);
+    e = launch_plan(a, fwd_variant(active_variant()).cc, st);
     if (e != cudaSuccess) return cuda_fail(e, "plan launch");
   }
   if (!(params->flags & CF_FLAG_PLAN_ONLY)) {
-    e = launch_forward(a, 0, (params->flags & CF_FLAG_PER_PAIR_LAUNCH) != 0, st);
+    e = launch_forward(a, active_variant(), (params->flags & CF_FLAG_PER_PAIR_LAUNCH) != 0, st);
     if (e != cudaSuccess) return cuda_fail(e, "forward launch");
   }
   return ok();
@@ -464,7 +477,7 @@ cf_status cf_match(const void* d_pack_a, const void* d_pack_b, const int32_t* d_
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaMemsetAsync(d_ws, 0, sizeof(WsHeader), st);
   if (e != cudaSuccess) return cuda_fail(e, "workspace reset");
-  e = launch_plan(a, fwd_variant(0).cc, st);
+  e = launch_plan(a, fwd_variant(active_variant()).cc, st);
   if (e != cudaSuccess) return cuda_fail(e, "plan launch");
   e = launch_match_only(a, st);
   if (e != cudaSuccess) return cuda_fail(e, "match launch");

@@ -1,24 +1,30 @@
 // a2-a7: the batched similarity forward, greedy matching and graph score.
 //
-// One persistent kernel drains three cost-ordered queues (filled by plan.cu):
-//   global class: pairs too large for shared memory; a CTA iterates X in a
-//                 per-CTA scratch slot of the workspace (L2-resident),
-//   CTA class:    a CTA keeps two iterates of X in shared memory,
-//   warp class:   each warp keeps a small pair in its own shared-memory slice.
+// One persistent kernel, one 1024-thread CTA per SM, drains four cost-ordered
+// queues (filled by plan.cu), largest work first:
+//   global class:  pairs too large for shared memory; the whole CTA iterates X
+//                  in a scratch slot of the workspace (L2-resident),
+//   CTA class:     the whole CTA keeps the pair in its 220 KB of shared memory,
+//   quarter class: four 256-thread groups (named barriers 1-4) each keep a
+//                  pair in their quarter of the shared memory,
+//   warp class:    every warp keeps a small pair in its own 1/32 slice.
+// A quarter group that finds its queue empty goes straight on to warp-class
+// pairs in its own slices, so the tail of one class overlaps the next.
+//
 // Iteration (Table 1 "Iso" row, IsoRank-style, renormalised every step):
 //   Y_{k+1} = alpha/2 (W_A X_k W_B^T + W_A^T X_k W_B) + (1 - alpha) Ehat,
 //   X_{k+1} = Y_{k+1} / |Y_{k+1}|_F.
 // The kernel stores Y (unnormalised) and carries s_k = 1/|Y_k|: because the
-// propagation is linear, Z(X_k) = s_k Z(Y_k), so the norm is only needed
-// after the gathers and each iteration has a single barrier (inside the
+// propagation is linear, Z(X_k) = s_k Z(Y_k), so the norm is only needed after
+// the gathers, and each iteration has a single group barrier (inside the
 // fused Frobenius-norm reduction) with Y double-buffered.
 //
-// Thread mapping of a shared-memory pair (see Shape in layout.h): thread g
-// owns column j = g % n_col of the resident matrix and rows r0 + R m.  The
-// column graph's adjacency lists of j (first two entries, the common CFG
-// degree) live in registers for the whole pair; the row graph's lists are
-// read through the read-only cache and are uniform across the lanes that
-// share a row.  Ehat of the owned entries stays in registers.
+// Thread mapping of a resident pair (Shape in layout.h): thread g owns column
+// j = g % n_col and rows r0 + R m.  The column graph's adjacency lists of j
+// (first two entries, the common CFG degree) live in registers for the whole
+// pair.  The row graph's lists are staged once per pair in shared memory as
+// per-row edge ranges and {u * ld, w} entries, so a gather is two dependent
+// shared loads and the lanes sharing a row read the same words.
 #include "device_common.cuh"
 #include "kernels.h"
 
@@ -60,14 +66,16 @@ struct Geo {
   const float* c_attr;
 };
 
-__device__ __forceinline__ Geo make_geo(const Ctx& cx, int p, const ClassCfg& cc) {
+__device__ __forceinline__ Geo make_geo(const Ctx& cx, int p, const ClassCfg& cc, int min_cls) {
   Geo g;
   g.p = p;
   const int pa = __ldg(cx.pairs + 2 * p), pb = __ldg(cx.pairs + 2 * p + 1);
   const int ba = __ldg(cx.A.node_off + pa), bb = __ldg(cx.B.node_off + pb);
   g.na = __ldg(cx.A.node_off + pa + 1) - ba;
   g.nb = __ldg(cx.B.node_off + pb + 1) - bb;
-  g.s = classify(g.na, g.nb, cc);
+  const int ea = __ldg(cx.A.edge_off + pa + 1) - __ldg(cx.A.edge_off + pa);
+  const int eb = __ldg(cx.B.edge_off + pb + 1) - __ldg(cx.B.edge_off + pb);
+  g.s = classify(g.na, g.nb, ea, eb, cc, min_cls);
   const PackView& R = g.s.tr ? cx.B : cx.A;
   const PackView& C = g.s.tr ? cx.A : cx.B;
   const int rb = g.s.tr ? bb : ba, cbse = g.s.tr ? ba : bb;
@@ -84,66 +92,150 @@ __device__ __forceinline__ Geo make_geo(const Ctx& cx, int p, const ClassCfg& cc
   return g;
 }
 
-// Adjacency lists of one column-graph block, first two entries in registers.
-struct ColLists {
-  int no, ni, vo0, vo1, vi0, vi1;
-  float wo0, wo1, wi0, wi1;
-  const CfAdj* po;
-  const CfAdj* pi;
+__device__ __forceinline__ void bar_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// A group of threads working on one pair: a single warp (bar < 0) or a set of
+// whole warps synchronised by named barrier `bar`.  sum() contains the
+// group's one barrier; `redf`/`redi` hold two parities of per-warp partials
+// so that consecutive sums need no second barrier.
+struct Group {
+  int rank, size, bar;
+  float* redf;
+  int* redi;
+  __device__ __forceinline__ int warp() const { return rank >> 5; }
+  __device__ __forceinline__ int nwarps() const { return size >> 5; }
+  __device__ __forceinline__ void sync() const {
+    if (bar < 0)
+      __syncwarp();
+    else
+      bar_sync(bar, size);
+  }
+  // Each warp writes its partial, then every warp reads all partials (one per
+  // lane) and reduces them with the same butterfly, so all threads get the
+  // same bits.
+  __device__ __forceinline__ float sum(float v, int par) const {
+    v = warp_sum(v);
+    if (bar < 0) {
+      __syncwarp();
+      return v;
+    }
+    const int lane = rank & 31;
+    if (lane == 0) redf[par * 32 + (rank >> 5)] = v;
+    bar_sync(bar, size);
+    return warp_sum(lane < (size >> 5) ? redf[par * 32 + lane] : 0.f);
+  }
+  __device__ __forceinline__ int sum_i(int v, int par) const {
+    v = warp_sum_i(v);
+    if (bar < 0) {
+      __syncwarp();
+      return v;
+    }
+    const int lane = rank & 31;
+    if (lane == 0) redi[par * 32 + (rank >> 5)] = v;
+    bar_sync(bar, size);
+    return warp_sum_i(lane < (size >> 5) ? redi[par * 32 + lane] : 0);
+  }
 };
 
-__device__ __forceinline__ ColLists load_col(const Geo& g, int j) {
-  ColLists c;
-  int e0 = __ldg(g.c_optr + j), e1 = __ldg(g.c_optr + j + 1);
-  c.no = e1 - e0;
-  c.po = g.c_oadj + e0;
-  CfAdj x = c.no > 0 ? ldg_adj(c.po) : CfAdj{0, 0.f};
-  c.vo0 = x.nbr;
-  c.wo0 = x.w;
-  x = c.no > 1 ? ldg_adj(c.po + 1) : CfAdj{0, 0.f};
-  c.vo1 = x.nbr;
-  c.wo1 = x.w;
-  e0 = __ldg(g.c_iptr + j);
-  e1 = __ldg(g.c_iptr + j + 1);
-  c.ni = e1 - e0;
-  c.pi = g.c_iadj + e0;
-  x = c.ni > 0 ? ldg_adj(c.pi) : CfAdj{0, 0.f};
-  c.vi0 = x.nbr;
-  c.wi0 = x.w;
-  x = c.ni > 1 ? ldg_adj(c.pi + 1) : CfAdj{0, 0.f};
-  c.vi1 = x.nbr;
-  c.wi1 = x.w;
+// Lists of one column-graph block j for the straight-line gather: its first
+// two out- and in-neighbours as byte offsets v * 4 with weights, missing
+// entries padded with {0, 0.0f}; the ranges of its further neighbours in the
+// staged column entries (empty for the common degree <= 2); flag != 0 when
+// there are any.
+struct ColPad {
+  int vo0, vo1, vi0, vi1;
+  float wo0, wo1, wi0, wi1;
+  int xo0, xo1, xi0, xi1;
+  int flag;
+};
+
+// cptr = the column graph's staged row pointers (out: [0, n_col], in: after
+// them, both local to its staged entries); cedge = its {v 4, w} entries.
+__device__ __forceinline__ ColPad load_col(const int* cptr, const int2* cedge, int n_col, int j) {
+  ColPad c;
+  const int e0 = cptr[j], e1 = cptr[j + 1];
+  int2 x = e1 > e0 ? cedge[e0] : make_int2(0, 0);
+  c.vo0 = x.x;
+  c.wo0 = __int_as_float(x.y);
+  x = e1 > e0 + 1 ? cedge[e0 + 1] : make_int2(0, 0);
+  c.vo1 = x.x;
+  c.wo1 = __int_as_float(x.y);
+  c.xo0 = e0 + 2;
+  c.xo1 = e1;
+  const int f0 = cptr[n_col + 1 + j], f1 = cptr[n_col + 2 + j];
+  x = f1 > f0 ? cedge[f0] : make_int2(0, 0);
+  c.vi0 = x.x;
+  c.wi0 = __int_as_float(x.y);
+  x = f1 > f0 + 1 ? cedge[f0 + 1] : make_int2(0, 0);
+  c.vi1 = x.x;
+  c.wi1 = __int_as_float(x.y);
+  c.xi0 = f0 + 2;
+  c.xi1 = f1;
+  c.flag = (e1 - e0 > 2 || f1 - f0 > 2) ? 1 : 0;
   return c;
 }
 
-// sum over the column block's neighbours v of w_v * row[v]
-__device__ __forceinline__ float dot_col(const float* row, int n, int v0, float w0, int v1, float w1,
-                                        const CfAdj* p) {
-  float t = 0.f;
-  if (n > 0) t = w0 * row[v0];
-  if (n > 1) t = fmaf(w1, row[v1], t);
-  for (int f = 2; f < n; ++f) {
-    CfAdj a = ldg_adj(p + f);
-    t = fmaf(a.w, row[a.nbr], t);
-  }
-  return t;
+__device__ __forceinline__ float lds_at(const char* base, int byte_off) {
+  return *reinterpret_cast<const float*>(base + byte_off);
 }
 
-// Successor-pair sum plus predecessor-pair sum for entry (i, j):
-//   sum_{i->u} sum_{j->v} w_iu w_jv Y[u,v] + sum_{u->i} sum_{v->j} w_ui w_vj Y[u,v]
-__device__ __forceinline__ float gather_s(const float* Y, int ld, const Geo& g, int i, const ColLists& c) {
+// Entry (i, j) of  sum_{i->u} sum_{j->v} w_iu w_jv Y[u,v] + sum_{u->i} sum_{v->j} w_ui w_vj Y[u,v]
+// is split over the neighbour pairs as
+//   (first two of i) x (first two of j)      gather_fast: straight-line, eight loads
+// + (further ones of i) x (first two of j)   row_extra: same trip count for the lanes of row i
+// + (all of i) x (further ones of j)         col_extra: only lanes whose column has them
+// which covers every pair exactly once.  A = row i's first two out-neighbours
+// {u ld 4, w} (the sign bit of A.w flags further neighbours of i), Q = its
+// first two in-neighbours; padding entries carry weight 0.
+__device__ __forceinline__ float gather_fast(const char* Y, const int4 A, const int4 Q, const ColPad& c) {
+  const float a0 = lds_at(Y, A.x + c.vo0), a1 = lds_at(Y, A.x + c.vo1);
+  const float a2 = lds_at(Y, A.z + c.vo0), a3 = lds_at(Y, A.z + c.vo1);
+  const float b0 = lds_at(Y, Q.x + c.vi0), b1 = lds_at(Y, Q.x + c.vi1);
+  const float b2 = lds_at(Y, Q.z + c.vi0), b3 = lds_at(Y, Q.z + c.vi1);
+  const float so =
+      fmaf(fabsf(__int_as_float(A.w)), fmaf(c.wo1, a3, c.wo0 * a2), __int_as_float(A.y) * fmaf(c.wo1, a1, c.wo0 * a0));
+  const float si =
+      fmaf(__int_as_float(Q.w), fmaf(c.wi1, b3, c.wi0 * b2), __int_as_float(Q.y) * fmaf(c.wi1, b1, c.wi0 * b0));
+  return so + si;
+}
+
+// rr = row i's full out- and in-edge ranges into redge ({u ld 4, w}).
+__device__ __forceinline__ float row_extra(const char* Y, const int4 rr, const int2* redge, const ColPad& c) {
   float s = 0.f;
-  int e = __ldg(g.r_optr + i);
-  const int e1 = __ldg(g.r_optr + i + 1);
-  for (; e < e1; ++e) {
-    const CfAdj a = ldg_adj(g.r_oadj + e);
-    s = fmaf(a.w, dot_col(Y + a.nbr * ld, c.no, c.vo0, c.wo0, c.vo1, c.wo1, c.po), s);
+  for (int k = rr.x + 2; k < rr.y; ++k) {
+    const int2 e = redge[k];
+    s = fmaf(__int_as_float(e.y), fmaf(c.wo1, lds_at(Y, e.x + c.vo1), c.wo0 * lds_at(Y, e.x + c.vo0)), s);
   }
-  int f = __ldg(g.r_iptr + i);
-  const int f1 = __ldg(g.r_iptr + i + 1);
-  for (; f < f1; ++f) {
-    const CfAdj a = ldg_adj(g.r_iadj + f);
-    s = fmaf(a.w, dot_col(Y + a.nbr * ld, c.ni, c.vi0, c.wi0, c.vi1, c.wi1, c.pi), s);
+  for (int k = rr.z + 2; k < rr.w; ++k) {
+    const int2 e = redge[k];
+    s = fmaf(__int_as_float(e.y), fmaf(c.wi1, lds_at(Y, e.x + c.vi1), c.wi0 * lds_at(Y, e.x + c.vi0)), s);
+  }
+  return s;
+}
+
+// cedge = the column graph's staged {v 4, w} entries (out-edges, then in-edges).
+__device__ __forceinline__ float col_extra(const char* Y, const int4 A, const int4 Q, const int4 rr,
+                                           const int2* redge, const int2* cedge, const ColPad& c) {
+  float s = 0.f;
+  for (int f = c.xo0; f < c.xo1; ++f) {
+    const int2 v = cedge[f];
+    float t = fmaf(fabsf(__int_as_float(A.w)), lds_at(Y, A.z + v.x), __int_as_float(A.y) * lds_at(Y, A.x + v.x));
+    for (int k = rr.x + 2; k < rr.y; ++k) {
+      const int2 e = redge[k];
+      t = fmaf(__int_as_float(e.y), lds_at(Y, e.x + v.x), t);
+    }
+    s = fmaf(__int_as_float(v.y), t, s);
+  }
+  for (int f = c.xi0; f < c.xi1; ++f) {
+    const int2 v = cedge[f];
+    float t = fmaf(__int_as_float(Q.w), lds_at(Y, Q.z + v.x), __int_as_float(Q.y) * lds_at(Y, Q.x + v.x));
+    for (int k = rr.z + 2; k < rr.w; ++k) {
+      const int2 e = redge[k];
+      t = fmaf(__int_as_float(e.y), lds_at(Y, e.x + v.x), t);
+    }
+    s = fmaf(__int_as_float(v.y), t, s);
   }
   return s;
 }
@@ -176,18 +268,34 @@ __device__ __forceinline__ float gather_g(const float* Y, int ld, const Geo& g, 
   return s;
 }
 
-__device__ __forceinline__ float attr_norm(const float* a, const float* om, int F) {
+// Weighted attribute norm sqrt(sum_f w_f a_f^2) and weighted dot product
+// sum_f w_f a_f b_f over the zero-padded F_pad columns, four at a time.
+__device__ __forceinline__ float attr_norm(const float* a, const float* om, int Fp) {
+  const float4* a4 = reinterpret_cast<const float4*>(a);
+  const float4* o4 = reinterpret_cast<const float4*>(om);
   float acc = 0.f;
-  for (int f = 0; f < F; ++f) {
-    const float v = __ldg(a + f);
-    acc = fmaf(om[f] * v, v, acc);
+  for (int q = 0; q < (Fp >> 2); ++q) {
+    const float4 v = __ldg(a4 + q), w = o4[q];
+    acc = fmaf(w.x * v.x, v.x, acc);
+    acc = fmaf(w.y * v.y, v.y, acc);
+    acc = fmaf(w.z * v.z, v.z, acc);
+    acc = fmaf(w.w * v.w, v.w, acc);
   }
   return sqrtf(acc);
 }
 
-__device__ __forceinline__ float attr_dot(const float* a, const float* b, const float* om, int F) {
+__device__ __forceinline__ float attr_dot(const float* a, const float* b, const float* om, int Fp) {
+  const float4* a4 = reinterpret_cast<const float4*>(a);
+  const float4* b4 = reinterpret_cast<const float4*>(b);
+  const float4* o4 = reinterpret_cast<const float4*>(om);
   float acc = 0.f;
-  for (int f = 0; f < F; ++f) acc = fmaf(om[f] * __ldg(a + f), __ldg(b + f), acc);
+  for (int q = 0; q < (Fp >> 2); ++q) {
+    const float4 u = __ldg(a4 + q), v = __ldg(b4 + q), w = o4[q];
+    acc = fmaf(w.x * u.x, v.x, acc);
+    acc = fmaf(w.y * u.y, v.y, acc);
+    acc = fmaf(w.z * u.z, v.z, acc);
+    acc = fmaf(w.w * u.w, v.w, acc);
+  }
   return acc;
 }
 
@@ -199,16 +307,24 @@ __device__ __forceinline__ float attr_dot(const float* a, const float* b, const 
 // greedy, so matching every such entry at once and repeating gives the same
 // matching.  Within a row the order reduces to (value desc, column asc) and
 // within a column to (value desc, row asc) in either orientation.
-// State per row/column: >= 0 best live partner, -2 stale, -1 no candidate
-// (only with NaN entries), <= -3 matched to (-3 - v).  Every round matches at
-// least one pair for finite X, so the loop is bounded by min(n_row, n_col)
-// rounds; if that bound is reached without a full matching (NaN in X) the
-// status word gets CF_ERR_NUMERIC.  Returns the score on every thread; writes
-// match[n_a] if given.
-template <class Grp, class IdxT>
-__device__ float greedy(const Grp grp, const float* X, int ld, int n_row, int n_col, int tr, IdxT* rb,
-                        IdxT* nm, IdxT* cb, float* redf, int* redi, int32_t* mo, WsHeader* hdr, int pidx) {
-  const int t = grp.rank(), G = Grp::size(), lane = t & 31, w = grp.warp(), NW = Grp::nwarps();
+//
+// State per row (rb) and column (cb): >= 0 best live partner, -2 not yet
+// computed, -1 no candidate (only with NaN entries), <= -3 matched to -3 - v.
+// A round has two barriers:
+//   A  every live row whose best column died (or was never computed) rescans
+//      the live columns, and every such column rescans the live rows (a warp
+//      per row / column).  Liveness changes only in B, so these scans agree.
+//   B  every row whose best column names it back is matched; the round's
+//      matches are counted by a group sum.  A row's entry is written only by
+//      its own thread, a column's only by the thread of the row it names.
+// Every round matches at least one pair for finite X (the largest live entry
+// is locally dominant), so the loop is bounded by min(n_row, n_col) rounds; if
+// the bound is reached first (NaN in X) the status word gets CF_ERR_NUMERIC.
+// Returns the score on every thread; writes match[n_a] if given.
+template <class IdxT>
+__device__ __forceinline__ float greedy(const Group& grp, const float* X, int ld, int n_row, int n_col, int tr,
+                                        IdxT* rb, IdxT* cb, int32_t* mo, WsHeader* hdr, int pidx) {
+  const int t = grp.rank, G = grp.size, lane = t & 31, w = grp.warp(), NW = grp.nwarps();
   for (int r = t; r < n_row; r += G) rb[r] = (IdxT)-2;
   for (int c = t; c < n_col; c += G) cb[c] = (IdxT)-2;
   grp.sync();
@@ -216,31 +332,32 @@ __device__ float greedy(const Grp grp, const float* X, int ld, int n_row, int n_
   int matched = 0, par = 0;
   for (int round = 0; matched < need && round < need; ++round) {
     for (int r = w; r < n_row; r += NW) {
-      if (rb[r] != (IdxT)-2) continue;
+      const int v = rb[r];
+      if (!(v == -2 || (v >= 0 && cb[v] <= (IdxT)-3))) continue;
       float bv = -CUDART_INF_F;
       int bi = 0x7fffffff;
       const float* xr = X + (size_t)r * ld;
       for (int c = lane; c < n_col; c += 32)
         if (cb[c] > (IdxT)-3) {
-          const float v = xr[c];
-          if (v > bv) {
-            bv = v;
+          const float x = xr[c];
+          if (x > bv) {
+            bv = x;
             bi = c;
           }
         }
       warp_argmax(bv, bi);
       if (lane == 0) rb[r] = bi == 0x7fffffff ? (IdxT)-1 : (IdxT)bi;
     }
-    grp.sync();
     for (int c = w; c < n_col; c += NW) {
-      if (cb[c] != (IdxT)-2) continue;
+      const int v = cb[c];
+      if (!(v == -2 || (v >= 0 && rb[v] <= (IdxT)-3))) continue;
       float bv = -CUDART_INF_F;
       int bi = 0x7fffffff;
       for (int r = lane; r < n_row; r += 32)
         if (rb[r] > (IdxT)-3) {
-          const float v = X[(size_t)r * ld + c];
-          if (v > bv) {
-            bv = v;
+          const float x = X[(size_t)r * ld + c];
+          if (x > bv) {
+            bv = x;
             bi = r;
           }
         }
@@ -248,34 +365,19 @@ __device__ float greedy(const Grp grp, const float* X, int ld, int n_row, int n_
       if (lane == 0) cb[c] = bi == 0x7fffffff ? (IdxT)-1 : (IdxT)bi;
     }
     grp.sync();
-    for (int r = t; r < n_row; r += G) {
-      const int c = rb[r];
-      nm[r] = (c >= 0 && cb[c] == r) ? (IdxT)c : (IdxT)-1;
-    }
-    grp.sync();
     int nn = 0;
     for (int r = t; r < n_row; r += G) {
-      const int c = nm[r];
-      if (c >= 0) {
+      const int c = rb[r];
+      if (c >= 0 && cb[c] == r) {
         rb[r] = (IdxT)(-3 - c);
         cb[c] = (IdxT)(-3 - r);
         ++nn;
       }
     }
-    matched += grp.sum_i(nn, redi, par);
+    matched += grp.sum_i(nn, par);
     par ^= 1;
-    for (int r = t; r < n_row; r += G) {
-      const int c = rb[r];
-      if (c >= 0 && cb[c] <= (IdxT)-3) rb[r] = (IdxT)-2;
-    }
-    grp.sync();
-    for (int c = t; c < n_col; c += G) {
-      const int r = cb[c];
-      if (r >= 0 && rb[r] <= (IdxT)-3) cb[c] = (IdxT)-2;
-    }
-    grp.sync();
   }
-  if (matched < need && grp.rank() == 0 && hdr) set_status(hdr, 6 /* CF_ERR_NUMERIC */, pidx);
+  if (matched < need && t == 0 && hdr) set_status(hdr, 6 /* CF_ERR_NUMERIC */, pidx);
   float sc = 0.f;
   if (!tr) {
     for (int r = t; r < n_row; r += G) {
@@ -292,54 +394,201 @@ __device__ float greedy(const Grp grp, const float* X, int ld, int n_row, int n_
       if (mo) mo[c] = r;
     }
   }
-  return grp.sum(sc, redf, 0);
+  return grp.sum(sc, 0);
+}
+
+// a5-a6 for shared-memory-resident pairs: the same rounds of locally
+// dominant entries as greedy(), but every row's columns and every column's
+// rows are ranked once (value desc, index asc; the within-row and
+// within-column parts of the greedy order), so finding a row's best live
+// column is a cursor advance past dead entries of its ranked list instead of
+// a rescan.  One thread per row / column, two group barriers per round.
+// rs: ranked columns of each row [n_row][n_col], cs: ranked rows of each
+// column [n_col][n_row] (int16); cursors, bests and dead flags per row and
+// column.  An entry written by no rank (NaN in X) is skipped as dead.
+__device__ __forceinline__ float greedy_ranked(const Group& grp, const float* X, int ld, int n_row, int n_col,
+                                               int tr, int16_t* rs, int16_t* cs, unsigned char* st, int32_t* mo,
+                                               WsHeader* hdr, int pidx) {
+  const int t = grp.rank, G = grp.size;
+  int16_t* rcur = reinterpret_cast<int16_t*>(st);
+  int16_t* ccur = rcur + n_row;
+  int16_t* rbest = ccur + n_col;
+  int16_t* cbest = rbest + n_row;
+  unsigned char* rdead = reinterpret_cast<unsigned char*>(cbest + n_col);
+  unsigned char* cdead = rdead + n_row;
+  const int E = n_row * n_col;
+  for (int idx = t; idx < E; idx += G) {
+    const int r = idx / n_col, c = idx - r * n_col;
+    const float* xr = X + (size_t)r * ld;
+    const float x = xr[c];
+    int kr = 0;
+    for (int c2 = 0; c2 < n_col; ++c2) {
+      const float y = xr[c2];
+      kr += (y > x) | ((y == x) & (c2 < c));
+    }
+    int kc = 0;
+    for (int r2 = 0; r2 < n_row; ++r2) {
+      const float y = X[(size_t)r2 * ld + c];
+      kc += (y > x) | ((y == x) & (r2 < r));
+    }
+    if (kr < n_col) rs[r * n_col + kr] = (int16_t)c;
+    if (kc < n_row) cs[c * n_row + kc] = (int16_t)r;
+  }
+  for (int r = t; r < n_row; r += G) {
+    rcur[r] = 0;
+    rdead[r] = 0;
+  }
+  for (int c = t; c < n_col; c += G) {
+    ccur[c] = 0;
+    cdead[c] = 0;
+  }
+  grp.sync();
+  const int need = min(n_row, n_col);
+  int matched = 0, par = 0;
+  for (int round = 0; matched < need && round < need; ++round) {
+    for (int r = t; r < n_row; r += G) {
+      if (rdead[r]) continue;
+      int k = rcur[r], c = -1;
+      for (; k < n_col; ++k) {
+        const int v = rs[r * n_col + k];
+        if ((unsigned)v < (unsigned)n_col && !cdead[v]) {
+          c = v;
+          break;
+        }
+      }
+      rcur[r] = (int16_t)k;
+      rbest[r] = (int16_t)c;
+    }
+    for (int c = t; c < n_col; c += G) {
+      if (cdead[c]) continue;
+      int k = ccur[c], r = -1;
+      for (; k < n_row; ++k) {
+        const int v = cs[c * n_row + k];
+        if ((unsigned)v < (unsigned)n_row && !rdead[v]) {
+          r = v;
+          break;
+        }
+      }
+      ccur[c] = (int16_t)k;
+      cbest[c] = (int16_t)r;
+    }
+    grp.sync();
+    int nn = 0;
+    for (int r = t; r < n_row; r += G) {
+      if (rdead[r]) continue;
+      const int c = rbest[r];
+      if (c >= 0 && cbest[c] == r) {
+        rdead[r] = 1;
+        cdead[c] = 1;
+        ++nn;
+      }
+    }
+    matched += grp.sum_i(nn, par);
+    par ^= 1;
+  }
+  if (matched < need && t == 0 && hdr) set_status(hdr, 6 /* CF_ERR_NUMERIC */, pidx);
+  float sc = 0.f;
+  for (int r = t; r < n_row; r += G)
+    if (rdead[r]) sc += X[(size_t)r * ld + rbest[r]];
+  if (mo) {
+    if (!tr)
+      for (int r = t; r < n_row; r += G) mo[r] = rdead[r] ? rbest[r] : -1;
+    else
+      for (int c = t; c < n_col; c += G) mo[c] = cdead[c] ? cbest[c] : -1;
+  }
+  return grp.sum(sc, 0);
 }
 
 // Write X_K (resident, possibly transposed, stride ld) to the caller's
 // row-major n_a x n_b output, coalesced on the global side.
-template <class Grp>
-__device__ __forceinline__ void store_x(const Grp grp, const Ctx& cx, const Geo& g, const float* Xs, int ld) {
+__device__ __forceinline__ void store_x(const Group& grp, const Ctx& cx, const Geo& g, const float* Xs, int ld) {
   float* dst = cx.X + cx.x_off[g.p];
   const int tot = g.na * g.nb;
-  for (int idx = grp.rank(); idx < tot; idx += Grp::size()) {
+  for (int idx = grp.rank; idx < tot; idx += grp.size) {
     const int ia = idx / g.nb, jb = idx - ia * g.nb;
     const int r = g.s.tr ? jb : ia, c = g.s.tr ? ia : jb;
     dst[idx] = Xs[(size_t)r * ld + c];
   }
 }
 
-// A shared-memory-resident pair on a warp or a CTA.  buf0/buf1 hold the two
-// iterates Y_k, Y_{k+1}; ehb holds (1 - alpha) Ehat.  Each thread reads and
-// writes only its own entries of ehb, so ehb needs no barrier.
-template <class Grp>
-__device__ __forceinline__ void run_pair_s(const Ctx& cx, const Geo& g, const Grp grp, float* buf0, float* buf1,
-                                           float* ehb, int16_t* ms, float* redf, int* redi) {
+// A shared-memory-resident pair on a group.  Region layout (bytes):
+//   [ (1-alpha) Ehat | Y0 | Y1 ]  3 x n_row*ld floats,
+//   [ ra ]  int4 per row: first two out-neighbours {u ld 4, w}, padded; the
+//           sign bit of the last word flags a row with > 2 out- or in-neighbours,
+//   [ rq ]  int4 per row: first two in-neighbours, padded,
+//   [ rr ]  int4 per row: its full out- and in-edge ranges into redge,
+//   [ redge ] {u ld 4, w}: the row graph's out-edges, then in-edges,
+//   [ cedge ] {v 4, w}: the column graph's out-edges, then in-edges,
+//   [ cptr ]  the column graph's out- then in-row pointers into cedge.
+// After the iterations the Ehat buffer holds the row matching state and the
+// free iterate the column state (int16).
+__device__ __forceinline__ void run_pair_s(const Ctx& cx, const Geo& g, const Group& grp, unsigned char* region) {
   const Shape& s = g.s;
-  const int t = grp.rank();
+  const int t = grp.rank;
+  const int ld = s.ld;
+  const int nn = s.n_row * ld;
+  float* ehb = reinterpret_cast<float*>(region);
+  float* buf0 = ehb + nn;
+  float* buf1 = buf0 + nn;
+  int4* ra = reinterpret_cast<int4*>(region + align_up(12 * (size_t)nn, 16));
+  int4* rq = ra + s.n_row;
+  int4* rr = rq + s.n_row;
+  int2* redge = reinterpret_cast<int2*>(rr + s.n_row);
+
+  // stage the row graph and the column graph's entries
+  const int eo0 = __ldg(g.r_optr), ei0 = __ldg(g.r_iptr);
+  const int e_row = __ldg(g.r_optr + s.n_row) - eo0;
+  const int co0 = __ldg(g.c_optr), ci0 = __ldg(g.c_iptr);
+  const int e_col = __ldg(g.c_optr + s.n_col) - co0;
+  int2* cedge = redge + 2 * e_row;
+  int* cptr = reinterpret_cast<int*>(cedge + 2 * e_col);
+  for (int k = t; k < e_col; k += grp.size) {
+    const CfAdj a = ldg_adj(g.c_oadj + co0 + k), b = ldg_adj(g.c_iadj + ci0 + k);
+    cedge[k] = make_int2(4 * a.nbr, __float_as_int(a.w));
+    cedge[e_col + k] = make_int2(4 * b.nbr, __float_as_int(b.w));
+  }
+  for (int k = t; k <= s.n_col; k += grp.size) {
+    cptr[k] = __ldg(g.c_optr + k) - co0;
+    cptr[s.n_col + 1 + k] = e_col + __ldg(g.c_iptr + k) - ci0;
+  }
+  for (int i = t; i < s.n_row; i += grp.size) {
+    const int o0 = __ldg(g.r_optr + i) - eo0, o1 = __ldg(g.r_optr + i + 1) - eo0;
+    const int q0 = __ldg(g.r_iptr + i) - ei0, q1 = __ldg(g.r_iptr + i + 1) - ei0;
+    const CfAdj z{0, 0.f};
+    const CfAdj a0 = o1 > o0 ? ldg_adj(g.r_oadj + eo0 + o0) : z, a1 = o1 > o0 + 1 ? ldg_adj(g.r_oadj + eo0 + o0 + 1) : z;
+    const CfAdj b0 = q1 > q0 ? ldg_adj(g.r_iadj + ei0 + q0) : z, b1 = q1 > q0 + 1 ? ldg_adj(g.r_iadj + ei0 + q0 + 1) : z;
+    const int flag = (o1 - o0 > 2 || q1 - q0 > 2) ? (int)0x80000000 : 0;
+    ra[i] = make_int4(4 * ld * a0.nbr, __float_as_int(a0.w), 4 * ld * a1.nbr, __float_as_int(a1.w) | flag);
+    rq[i] = make_int4(4 * ld * b0.nbr, __float_as_int(b0.w), 4 * ld * b1.nbr, __float_as_int(b1.w));
+    rr[i] = make_int4(o0, o1, e_row + q0, e_row + q1);
+  }
+  for (int k = t; k < e_row; k += grp.size) {
+    const CfAdj a = ldg_adj(g.r_oadj + eo0 + k), b = ldg_adj(g.r_iadj + ei0 + k);
+    redge[k] = make_int2(4 * ld * a.nbr, __float_as_int(a.w));
+    redge[e_row + k] = make_int2(4 * ld * b.nbr, __float_as_int(b.w));
+  }
+  // a2: weighted attribute norms of the row blocks (buf1 is free until k = 0)
+  for (int i = t; i < s.n_row; i += grp.size) buf1[i] = attr_norm(g.r_attr + (size_t)i * cx.Fp, cx.om, cx.Fp);
   const bool act = t < s.R * s.n_col;
   const int j = act ? t % s.n_col : 0;
   const int r0 = act ? t / s.n_col : 0;
   const int Mt = (act && s.n_row > r0) ? ceil_div(s.n_row - r0, s.R) : 0;
-  const int ld = s.ld;
   const int step = s.R * ld;
   const int off0 = r0 * ld + j;
-
-  // a2: weighted attribute norms of the row blocks (buf1 is free until k = 0)
-  for (int i = t; i < s.n_row; i += Grp::size()) buf1[i] = attr_norm(g.r_attr + (size_t)i * cx.Fp, cx.om, cx.F);
   const float* bcol = g.c_attr + (size_t)j * cx.Fp;
-  const float cj = attr_norm(bcol, cx.om, cx.F);
+  const float cj = attr_norm(bcol, cx.om, cx.Fp);
   grp.sync();
 
   // a3: cosine attribute term E, its Frobenius norm, Ehat = X_0
   float ss = 0.f;
   for (int m = 0, i = r0, off = off0; m < Mt; ++m, i += s.R, off += step) {
-    const float dot = attr_dot(g.r_attr + (size_t)i * cx.Fp, bcol, cx.om, cx.F);
+    const float dot = attr_dot(g.r_attr + (size_t)i * cx.Fp, bcol, cx.om, cx.Fp);
     const float den = buf1[i] * cj;
     const float e = den > 0.f ? dot / den : 0.f;
     ehb[off] = e;
     ss = fmaf(e, e, ss);
   }
-  const float tot = grp.sum(ss, redf, 0);
+  const float tot = grp.sum(ss, 0);
   const float inv = tot > 0.f ? 1.0f / sqrtf(tot) : 0.f;
   const float uni = 1.0f / sqrtf((float)s.n_row * (float)s.n_col);
   const float cb = 1.f - cx.alpha;
@@ -348,25 +597,34 @@ __device__ __forceinline__ void run_pair_s(const Ctx& cx, const Geo& g, const Gr
     buf0[off] = eh;
     ehb[off] = cb * eh;
   }
-  const ColLists cl = load_col(g, j);
-  grp.sync();
+  grp.sync();  // staged column pointers visible
+  const ColPad cl = load_col(cptr, cedge, s.n_col, j);
 
   // a4: K renormalised iterations, one barrier each
   float sk = 1.f;
   for (int k = 0; k < cx.K; ++k) {
-    const float* cur = (k & 1) ? buf1 : buf0;
+    const char* cur = reinterpret_cast<const char*>((k & 1) ? buf1 : buf0);
     float* nxt = (k & 1) ? buf0 : buf1;
     const float ca = 0.5f * cx.alpha * sk;
     ss = 0.f;
+#pragma unroll 2
     for (int m = 0, i = r0, off = off0; m < Mt; ++m, i += s.R, off += step) {
-      const float y = fmaf(ca, gather_s(cur, ld, g, i, cl), ehb[off]);
+      const int4 A = ra[i], Q = rq[i];
+      float z = gather_fast(cur, A, Q, cl);
+      if (A.w < 0 || cl.flag) {
+        const int4 R4 = rr[i];
+        if (A.w < 0) z += row_extra(cur, R4, redge, cl);
+        if (cl.flag) z += col_extra(cur, A, Q, R4, redge, cedge, cl);
+      }
+      const float y = fmaf(ca, z, ehb[off]);
       nxt[off] = y;
       ss = fmaf(y, y, ss);
     }
-    const float yy = grp.sum(ss, redf, (k + 1) & 1);
+    const float yy = grp.sum(ss, (k + 1) & 1);
     sk = cx.norm_mode == 0 ? 1.0f / sqrtf(yy) : 1.f;
   }
   float* Xs = (cx.K & 1) ? buf1 : buf0;
+  float* freeb = (cx.K & 1) ? buf0 : buf1;
   if (sk != 1.f)
     for (int m = 0, off = off0; m < Mt; ++m, off += step) Xs[off] *= sk;
   grp.sync();
@@ -374,17 +632,23 @@ __device__ __forceinline__ void run_pair_s(const Ctx& cx, const Geo& g, const Gr
   if (cx.X) store_x(grp, cx, g, Xs, ld);
   if (cx.scores || cx.match) {
     int32_t* mo = cx.match ? cx.match + cx.m_off[g.p] : nullptr;
-    const float sc = greedy<Grp, int16_t>(grp, Xs, ld, s.n_row, s.n_col, s.tr, ms, ms + s.n_row,
-                                          ms + 2 * s.n_row, redf, redi, mo, cx.hdr, g.p);
-    if (cx.scores && t == 0) cx.scores[g.p] = sc;
+    if (5 * (size_t)(s.n_row + s.n_col) + 16 <= 4 * (size_t)nn) {  // room for the ranked lists' state
+      const float sc = greedy_ranked(grp, Xs, ld, s.n_row, s.n_col, s.tr, reinterpret_cast<int16_t*>(ehb),
+                                     reinterpret_cast<int16_t*>(ehb) + s.n_row * s.n_col,
+                                     reinterpret_cast<unsigned char*>(freeb), mo, cx.hdr, g.p);
+      if (cx.scores && t == 0) cx.scores[g.p] = sc;
+    } else {
+      const float sc = greedy<int16_t>(grp, Xs, ld, s.n_row, s.n_col, s.tr, reinterpret_cast<int16_t*>(ehb),
+                                       reinterpret_cast<int16_t*>(freeb), mo, cx.hdr, g.p);
+      if (cx.scores && t == 0) cx.scores[g.p] = sc;
+    }
   }
   grp.sync();
 }
 
-// A global-class pair on a CTA: X, Ehat and the matching state in a scratch slot.
-template <int NT>
-__device__ void run_pair_g(const Ctx& cx, const Geo& g, float* slot, float* redf, int* redi) {
-  const CtaGrp<NT> grp;
+// A global-class pair on the whole CTA: X, Ehat and the matching state in a
+// scratch slot of the workspace.
+__device__ __noinline__ void run_pair_g(const Ctx& cx, const Geo& g, const Group& grp, float* slot) {
   const int n_row = g.na, n_col = g.nb;  // global-class shapes are never transposed
   const int64_t E = (int64_t)n_row * n_col;
   float* b0 = slot;
@@ -393,28 +657,28 @@ __device__ void run_pair_g(const Ctx& cx, const Geo& g, float* slot, float* redf
   float* rn = eh + E;
   float* cn = rn + n_row;
   int32_t* ms = reinterpret_cast<int32_t*>(cn + n_col);
-  const int t = threadIdx.x;
-  for (int i = t; i < n_row; i += NT) rn[i] = attr_norm(g.r_attr + (size_t)i * cx.Fp, cx.om, cx.F);
-  for (int jj = t; jj < n_col; jj += NT) cn[jj] = attr_norm(g.c_attr + (size_t)jj * cx.Fp, cx.om, cx.F);
-  __syncthreads();
+  const int t = grp.rank, G = grp.size;
+  for (int i = t; i < n_row; i += G) rn[i] = attr_norm(g.r_attr + (size_t)i * cx.Fp, cx.om, cx.Fp);
+  for (int jj = t; jj < n_col; jj += G) cn[jj] = attr_norm(g.c_attr + (size_t)jj * cx.Fp, cx.om, cx.Fp);
+  grp.sync();
   float ss = 0.f;
-  for (int64_t idx = t; idx < E; idx += NT) {
+  for (int64_t idx = t; idx < E; idx += G) {
     const int i = (int)(idx / n_col), jj = (int)(idx - (int64_t)i * n_col);
-    const float dot = attr_dot(g.r_attr + (size_t)i * cx.Fp, g.c_attr + (size_t)jj * cx.Fp, cx.om, cx.F);
+    const float dot = attr_dot(g.r_attr + (size_t)i * cx.Fp, g.c_attr + (size_t)jj * cx.Fp, cx.om, cx.Fp);
     const float den = rn[i] * cn[jj];
     const float e = den > 0.f ? dot / den : 0.f;
     eh[idx] = e;
     ss = fmaf(e, e, ss);
   }
-  const float tot = grp.sum(ss, redf, 0);
+  const float tot = grp.sum(ss, 0);
   const float inv = tot > 0.f ? 1.0f / sqrtf(tot) : 0.f;
   const float uni = 1.0f / sqrtf((float)n_row * (float)n_col);
-  for (int64_t idx = t; idx < E; idx += NT) {
+  for (int64_t idx = t; idx < E; idx += G) {
     const float v = tot > 0.f ? eh[idx] * inv : uni;
     eh[idx] = v;
     b0[idx] = v;
   }
-  __syncthreads();
+  grp.sync();
   float sk = 1.f;
   const float cbl = 1.f - cx.alpha;
   for (int k = 0; k < cx.K; ++k) {
@@ -422,27 +686,26 @@ __device__ void run_pair_g(const Ctx& cx, const Geo& g, float* slot, float* redf
     float* nxt = (k & 1) ? b0 : b1;
     const float ca = 0.5f * cx.alpha * sk;
     ss = 0.f;
-    for (int64_t idx = t; idx < E; idx += NT) {
+    for (int64_t idx = t; idx < E; idx += G) {
       const int i = (int)(idx / n_col), jj = (int)(idx - (int64_t)i * n_col);
       const float y = fmaf(ca, gather_g(cur, n_col, g, i, jj), cbl * eh[idx]);
       nxt[idx] = y;
       ss = fmaf(y, y, ss);
     }
-    const float yy = grp.sum(ss, redf, (k + 1) & 1);
+    const float yy = grp.sum(ss, (k + 1) & 1);
     sk = cx.norm_mode == 0 ? 1.0f / sqrtf(yy) : 1.f;
   }
   float* Xs = (cx.K & 1) ? b1 : b0;
   if (sk != 1.f)
-    for (int64_t idx = t; idx < E; idx += NT) Xs[idx] *= sk;
-  __syncthreads();
+    for (int64_t idx = t; idx < E; idx += G) Xs[idx] *= sk;
+  grp.sync();
   if (cx.X) store_x(grp, cx, g, Xs, n_col);
   if (cx.scores || cx.match) {
     int32_t* mo = cx.match ? cx.match + cx.m_off[g.p] : nullptr;
-    const float sc = greedy<CtaGrp<NT>, int32_t>(grp, Xs, n_col, n_row, n_col, 0, ms, ms + n_row,
-                                                 ms + 2 * n_row, redf, redi, mo, cx.hdr, g.p);
+    const float sc = greedy<int32_t>(grp, Xs, n_col, n_row, n_col, 0, ms, ms + n_row, mo, cx.hdr, g.p);
     if (cx.scores && t == 0) cx.scores[g.p] = sc;
   }
-  __syncthreads();
+  grp.sync();
 }
 
 // Per-CTA setup, done by thread 0 into shared memory (so the pack views do
@@ -483,99 +746,90 @@ __device__ __forceinline__ bool make_ctx(const CallArgs& a, float* s_om, Ctx& cx
   return true;
 }
 
-// Shared-memory layout of the batched kernel: three buffers of ccap floats
-// (CTA class) which the warp class splits into NT/32 slices of three wcap
-// buffers; then the larger of the CTA tail (reduction partials and int16
-// matching state) and the warp tails (one matching state per warp).
-__host__ __device__ constexpr size_t msw_bytes(int warp_rows) { return (2 * (2 * warp_rows + 48) + 15) / 16 * 16; }
-__host__ __device__ constexpr size_t msc_bytes(int cta_rows, int nt) { return 512 + (2 * (2 * cta_rows + nt + 16) + 15) / 16 * 16; }
-__host__ __device__ constexpr size_t fwd_smem_bytes(int nt, int ccap, int warp_rows, int cta_rows) {
-  return 12 * (size_t)ccap + (msc_bytes(cta_rows, nt) > (size_t)(nt / 32) * msw_bytes(warp_rows)
-                                  ? msc_bytes(cta_rows, nt)
-                                  : (size_t)(nt / 32) * msw_bytes(warp_rows));
+// The persistent kernel's shapes: NT threads, one CTA per SM, 220 KB of
+// dynamic shared memory split 1 / 4 / (NT/32) ways for the three group levels.
+constexpr size_t kFwdSmem = 225280;
+template <int NT>
+__host__ __device__ constexpr ClassCfg fwd_cfg() {
+  return ClassCfg{NT, (int)kFwdSmem, (int)kFwdSmem / 4, (int)kFwdSmem / (NT / 32)};
 }
 
-template <int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB) fwd_batched_kernel(CallArgs a, ClassCfg cc, int per_pair) {
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) fwd_batched_kernel(CallArgs a, int per_pair) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ float s_om[kMaxF];
-  __shared__ uint32_t s_p;
+  __shared__ __align__(16) float s_om[kMaxF];
   __shared__ Ctx s_cx;
   __shared__ int s_ok;
+  __shared__ uint32_t s_p[1 + 4 + NT / 32];  // queue positions: CTA, quarter groups, warps
+  __shared__ float s_redf[5][64];       // partials of the CTA group and the four quarter groups
+  __shared__ int s_redi[5][64];
   if (!make_ctx(a, s_om, s_cx, &s_ok)) return;
   const Ctx& cx = s_cx;
-  float* buf0 = reinterpret_cast<float*>(smem);
-  float* buf1 = buf0 + cc.ccap;
-  float* ehb = buf1 + cc.ccap;
-  unsigned char* tail = smem + 12 * (size_t)cc.ccap;
-  float* redf = reinterpret_cast<float*>(tail);
-  int* redi = reinterpret_cast<int*>(tail + 256);
-  int16_t* ms_c = reinterpret_cast<int16_t*>(tail + 512);
-  const CtaGrp<NT> cta;
+  const ClassCfg cc = fwd_cfg<NT>();
+  const int t = threadIdx.x;
+  const Group cta{t, NT, 0, s_redf[0], s_redi[0]};
+  const bool single = per_pair >= 0;  // the plain form: one launch runs exactly one pair on the whole CTA
 
-  if (per_pair >= 0) {  // the plain form: this launch runs exactly one pair on the CTA
-    ClassCfg c1 = cc;
-    c1.warp_rows = 0;  // no warp class: the whole CTA takes the pair
-    const Geo g = make_geo(cx, per_pair, c1);
-    if (g.s.cls == kClassGlobal) {
-      const uint64_t need = global_slot_bytes(g.na, g.nb);
-      if (need > cx.scratch_bytes) {
-        if (threadIdx.x == 0) set_status(cx.hdr, 2 /* CF_ERR_WORKSPACE */, per_pair);
-        return;
-      }
-      run_pair_g<NT>(cx, g, reinterpret_cast<float*>(cx.scratch), redf, redi);
-    } else {
-      run_pair_s<CtaGrp<NT>>(cx, g, cta, buf0, buf1, ehb, ms_c, redf, redi);
-    }
-    return;
-  }
-
-  const uint32_t nG = cx.hdr->n_class[kClassGlobal];
-  const uint32_t nC = cx.hdr->n_class[kClassCta];
-  const uint32_t nWp = cx.hdr->n_class[kClassWarp];
-  // global class: one scratch slot per CTA
-  if (nG > 0) {
+  uint32_t n[kNumClasses];
+  for (int c = 0; c < kNumClasses; ++c) n[c] = single ? 0u : cx.hdr->n_class[c];
+  // global class: whole CTA, one scratch slot per CTA
+  if (n[kClassGlobal] > 0) {
     const uint64_t need = cx.hdr->slot_need;
     const uint64_t nslots = need ? cx.scratch_bytes / need : 0;
     if (nslots == 0) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) set_status(cx.hdr, 2 /* CF_ERR_WORKSPACE */, -1);
+      if (blockIdx.x == 0 && t == 0) set_status(cx.hdr, 2 /* CF_ERR_WORKSPACE */, -1);
     } else if (blockIdx.x < nslots) {
       float* slot = reinterpret_cast<float*>(cx.scratch + (size_t)blockIdx.x * need);
       for (;;) {
-        if (threadIdx.x == 0) s_p = atomicAdd(&cx.hdr->q_next[kClassGlobal], 1u);
+        if (t == 0) s_p[0] = atomicAdd(&cx.hdr->q_next[kClassGlobal], 1u);
         __syncthreads();
-        const uint32_t q = s_p;
+        const uint32_t q = s_p[0];
         __syncthreads();
-        if (q >= nG) break;
-        const Geo g = make_geo(cx, (int)cx.queue[q], cc);
-        run_pair_g<NT>(cx, g, slot, redf, redi);
+        if (q >= n[kClassGlobal]) break;
+        run_pair_g(cx, make_geo(cx, (int)cx.queue[q], cc, kClassWarp), cta, slot);
       }
     }
   }
-  // CTA class
-  for (;;) {
-    if (threadIdx.x == 0) s_p = atomicAdd(&cx.hdr->q_next[kClassCta], 1u);
-    __syncthreads();
-    const uint32_t q = s_p;
-    __syncthreads();
-    if (q >= nC) break;
-    const Geo g = make_geo(cx, (int)cx.queue[nG + q], cc);
-    run_pair_s<CtaGrp<NT>>(cx, g, cta, buf0, buf1, ehb, ms_c, redf, redi);
-  }
-  // warp class: every warp drains the queue on its own slice
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const WarpGrp wg{lane};
-  float* wb0 = buf0 + (size_t)w * 3 * cc.wcap;
-  float* wb1 = wb0 + cc.wcap;
-  float* web = wb1 + cc.wcap;
-  int16_t* ms_w = reinterpret_cast<int16_t*>(tail + (size_t)w * msw_bytes(cc.warp_rows));
-  for (;;) {
-    uint32_t q = 0;
-    if (lane == 0) q = atomicAdd(&cx.hdr->q_next[kClassWarp], 1u);
-    q = __shfl_sync(0xffffffffu, q, 0);
-    if (q >= nWp) break;
-    const Geo g = make_geo(cx, (int)cx.queue[nG + nC + q], cc);
-    run_pair_s<WarpGrp>(cx, g, wg, wb0, wb1, web, ms_w, nullptr, nullptr);
+  // shared-memory classes, one level after the other: the whole CTA, then
+  // four quarter groups (named barriers 1..4), then single warps.  Each level
+  // is a sub-partition of the previous one's region, and every group ends a
+  // pair with its own barrier, so no CTA-wide barrier sits between levels.
+  uint32_t qbase = n[kClassGlobal];
+  for (int level = kClassCta; level <= (single ? kClassCta : kClassWarp); ++level) {
+    Group grp = cta;
+    unsigned char* region = smem;
+    int slot = 0;
+    if (level == kClassQuarter) {
+      const int qg = t / (NT / 4);
+      grp = Group{t % (NT / 4), NT / 4, 1 + qg, s_redf[1 + qg], s_redi[1 + qg]};
+      region = smem + (size_t)qg * cc.z_qtr;
+      slot = 1 + qg;
+    } else if (level == kClassWarp) {
+      grp = Group{t & 31, 32, -1, nullptr, nullptr};
+      region = smem + (size_t)(t >> 5) * cc.z_wrp;
+      slot = 5 + (t >> 5);
+    }
+    const uint32_t count = single ? 1u : n[level];
+    for (;;) {
+      if (grp.rank == 0) s_p[slot] = single ? 0u : atomicAdd(&cx.hdr->q_next[level], 1u);
+      grp.sync();
+      const uint32_t q = s_p[slot];
+      grp.sync();
+      if (q >= count) break;
+      if (single && grp.rank == 0) s_p[slot] = 1u;  // the next pull ends the loop
+      const Geo g = make_geo(cx, single ? per_pair : (int)cx.queue[qbase + q], cc, single ? kClassCta : kClassWarp);
+      if (g.s.cls == kClassGlobal) {  // only in the plain form: scratch slot 0
+        if (global_slot_bytes(g.na, g.nb) > cx.scratch_bytes) {
+          if (t == 0) set_status(cx.hdr, 2 /* CF_ERR_WORKSPACE */, per_pair);
+        } else {
+          run_pair_g(cx, g, cta, reinterpret_cast<float*>(cx.scratch));
+        }
+        break;
+      }
+      run_pair_s(cx, g, grp, region);
+      if (single) break;
+    }
+    qbase += single ? 0u : n[level];
   }
 }
 
@@ -593,7 +847,7 @@ __global__ void __launch_bounds__(kMatchNT) match_only_kernel(CallArgs a) {
   const int64_t* m_off = reinterpret_cast<const int64_t*>(a.ws + L.m_off);
   WsHeader* hdr = reinterpret_cast<WsHeader*>(a.ws + L.hdr);
   int16_t* ms = reinterpret_cast<int16_t*>(smem);
-  const CtaGrp<kMatchNT> grp;
+  const Group grp{(int)threadIdx.x, kMatchNT, 0, redf, redi};
   for (int p = blockIdx.x; p < a.P; p += gridDim.x) {
     const int pa = a.pairs[2 * p], pb = a.pairs[2 * p + 1];
     if (pa < 0 || pa >= A.n_cfgs || pb < 0 || pb >= B.n_cfgs) continue;  // recorded by the plan
@@ -601,54 +855,55 @@ __global__ void __launch_bounds__(kMatchNT) match_only_kernel(CallArgs a) {
     const int nb = B.node_off[pb + 1] - B.node_off[pb];
     const float* X = a.X_in + x_off[p];
     int32_t* mo = a.match ? a.match + m_off[p] : nullptr;
-    const float sc = greedy<CtaGrp<kMatchNT>, int16_t>(grp, X, nb, na, nb, 0, ms, ms + na, ms + 2 * na, redf,
-                                                       redi, mo, hdr, p);
+    const float sc = greedy<int16_t>(grp, X, nb, na, nb, 0, ms, ms + na, mo, hdr, p);
     if (a.scores && threadIdx.x == 0) a.scores[p] = sc;
     __syncthreads();
   }
 }
 
-template <int NT, int MINB>
-struct Variant {
-  static cudaError_t launch(const CallArgs& a, const ClassCfg& cc, bool per_pair, cudaStream_t s) {
-    static int blocks_per_sm = -1, n_sm = 0;
-    const size_t sm = fwd_smem_bytes(NT, cc.ccap, cc.warp_rows, cc.cta_rows);
-    if (blocks_per_sm < 0) {
-      cudaError_t e =
-          cudaFuncSetAttribute(fwd_batched_kernel<NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      if (e != cudaSuccess) return e;
-      int dev = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, fwd_batched_kernel<NT, MINB>, NT, sm);
-      if (e != cudaSuccess) return e;
-      if (blocks_per_sm < 1) blocks_per_sm = 1;
-    }
-    if (per_pair) {
-      for (int p = 0; p < a.P; ++p) fwd_batched_kernel<NT, MINB><<<1, NT, sm, s>>>(a, cc, p);
-    } else {
-      fwd_batched_kernel<NT, MINB><<<blocks_per_sm * n_sm, NT, sm, s>>>(a, cc, -1);
-    }
-    return cudaGetLastError();
-  }
-};
+int g_n_sm = 0;
 
-// 256 threads, three CTAs per SM: 3 x 5632 floats per CTA (66 KB) + tails.
-constexpr ClassCfg kCfg0{256, 5632, 704, 256, 1024};
-using V0 = Variant<256, 3>;
+template <int NT>
+cudaError_t fwd_init() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e =
+      cudaFuncSetAttribute(fwd_batched_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, n = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  g_n_sm = n;
+  done = true;
+  return cudaSuccess;
+}
+
+template <int NT>
+cudaError_t launch_fwd(const CallArgs& a, bool per_pair, cudaStream_t s) {
+  cudaError_t e = fwd_init<NT>();
+  if (e != cudaSuccess) return e;
+  if (per_pair) {
+    for (int p = 0; p < a.P; ++p) fwd_batched_kernel<NT><<<1, NT, kFwdSmem, s>>>(a, p);
+  } else {
+    fwd_batched_kernel<NT><<<g_n_sm, NT, kFwdSmem, s>>>(a, -1);
+  }
+  return cudaGetLastError();
+}
 
 }  // namespace
 
-int num_fwd_variants() { return 1; }
+// Variants of the persistent forward kernel: 0 = 1024 threads (64 registers,
+// 32 warps per SM), 1 = 512 threads (128 registers, 16 warps per SM).
+int num_fwd_variants() { return 2; }
 
 FwdVariant fwd_variant(int v) {
-  (void)v;
-  return FwdVariant{kCfg0.nt, 0, 3, kCfg0};
+  return v == 1 ? FwdVariant{512, 0, 1, fwd_cfg<512>()} : FwdVariant{1024, 0, 1, fwd_cfg<1024>()};
 }
 
 cudaError_t launch_forward(const CallArgs& a, int variant, bool per_pair, cudaStream_t s) {
-  (void)variant;
-  return V0::launch(a, kCfg0, per_pair, s);
+  return variant == 1 ? launch_fwd<512>(a, per_pair, s) : launch_fwd<1024>(a, per_pair, s);
 }
 
 cudaError_t launch_match_only(const CallArgs& a, cudaStream_t s) {

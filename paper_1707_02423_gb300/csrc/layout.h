@@ -48,18 +48,27 @@ struct PackHeader {
   int64_t off_attr;     // float [n_blocks * F_pad]
 };
 
-// Execution classes of a pair, in queue order (largest work first).
-enum PairClass : int { kClassGlobal = 0, kClassCta = 1, kClassWarp = 2, kNumClasses = 3, kClassSkip = 3 };
+// Execution classes of a pair, in queue order (largest work first): the
+// global-memory tier, then the three shared-memory group levels of the
+// persistent kernel (whole CTA, quarter CTA, single warp).
+enum PairClass : int {
+  kClassGlobal = 0,
+  kClassCta = 1,
+  kClassQuarter = 2,
+  kClassWarp = 3,
+  kNumClasses = 4,
+  kClassSkip = 4
+};
 constexpr int kBuckets = 64;  // cost buckets per class (two per octave)
 
-// Tunable shape of the batched forward kernel.  The plan and the kernel
+// Shape of the batched forward kernel: threads per CTA and the shared-memory
+// region (bytes) a pair may use at each group level.  The plan and the kernel
 // classify pairs with the same values.
 struct ClassCfg {
-  int nt;         // threads per CTA
-  int ccap;       // floats per resident buffer of a CTA-class pair (n_row * ld)
-  int wcap;       // floats per resident buffer of a warp-class pair
-  int warp_rows;  // max rows of a warp-class pair (bounds the matching state)
-  int cta_rows;   // max rows of a CTA-class pair
+  int nt;     // threads per CTA (the CTA-level group)
+  int z_cta;  // region of the CTA-level group
+  int z_qtr;  // region of each of the four quarter groups (nt / 4 threads)
+  int z_wrp;  // region of each warp
 };
 
 // How a pair maps onto a group of G threads.  The "row" graph indexes the
@@ -72,26 +81,45 @@ struct Shape {
 
 CF_HD int pair_ld(int n_col) { return n_col | 1; }  // odd stride: column scans hit distinct banks
 
-CF_HD bool fits(int n_row, int n_col, int G, int rows_cap, int cap, int* R, int* M) {
-  if (n_col > G || n_row > rows_cap) return false;
-  *R = G / n_col;
-  *M = ceil_div(n_row, *R);
-  return (int64_t)n_row * pair_ld(n_col) <= cap;
+// Shared-memory bytes of a resident pair: (1 - alpha) Ehat and two iterates
+// (n_row x ld floats each); per row of the row graph its first two out- and
+// in-neighbours padded to two (two int4) and its full edge ranges (int4);
+// the row graph's out- then in-edge entries and the column graph's out- then
+// in-edge entries ({byte offset, w}, 8 bytes each); the column graph's out-
+// and in-edge row pointers (int32, n_col + 1 each).
+CF_HD size_t resident_bytes(int n_row, int ld, int e_row, int n_col, int e_col) {
+  return align_up(12 * (size_t)n_row * ld, 16) + 48 * (size_t)n_row + 16 * (size_t)e_row + 16 * (size_t)e_col +
+         align_up(8 * (size_t)(n_col + 1), 16);
 }
 
-// Smallest class that holds the pair, and the orientation with the fewest
-// rows per thread (ties: untransposed).
-CF_HD Shape classify(int na, int nb, const ClassCfg& c) {
+CF_HD bool fits(int n_row, int n_col, int e_row, int e_col, int G, size_t region, int* R, int* M) {
+  if (n_col > G) return false;
+  *R = G / n_col;
+  *M = ceil_div(n_row, *R);
+  return resident_bytes(n_row, pair_ld(n_col), e_row, n_col, e_col) <= region;
+}
+
+CF_HD int group_size(int cls, const ClassCfg& c) {
+  return cls == kClassWarp ? 32 : cls == kClassQuarter ? c.nt / 4 : c.nt;
+}
+
+CF_HD size_t group_region(int cls, const ClassCfg& c) {
+  return (size_t)(cls == kClassWarp ? c.z_wrp : cls == kClassQuarter ? c.z_qtr : c.z_cta);
+}
+
+// Smallest group level whose region holds the pair, with the orientation of
+// fewest rows per thread (ties: untransposed).  min_cls limits the levels
+// tried (kClassCta: the whole CTA only).
+CF_HD Shape classify(int na, int nb, int ea, int eb, const ClassCfg& c, int min_cls = kClassWarp) {
   Shape s{};
-  for (int cls = kClassWarp; cls >= kClassCta; --cls) {
-    int G = cls == kClassWarp ? 32 : c.nt;
-    int rows_cap = cls == kClassWarp ? c.warp_rows : c.cta_rows;
-    int cap = cls == kClassWarp ? c.wcap : c.ccap;
+  for (int cls = min_cls; cls >= kClassCta; --cls) {
+    const int G = group_size(cls, c);
+    const size_t Z = group_region(cls, c);
     int R0 = 0, M0 = 0, R1 = 0, M1 = 0;
-    bool f0 = fits(na, nb, G, rows_cap, cap, &R0, &M0);
-    bool f1 = fits(nb, na, G, rows_cap, cap, &R1, &M1);
+    const bool f0 = fits(na, nb, ea, eb, G, Z, &R0, &M0);
+    const bool f1 = fits(nb, na, eb, ea, G, Z, &R1, &M1);
     if (f0 || f1) {
-      bool tr = !f0 || (f1 && M1 < M0);
+      const bool tr = !f0 || (f1 && M1 < M0);
       s.cls = cls;
       s.tr = tr ? 1 : 0;
       s.n_row = tr ? nb : na;

@@ -60,7 +60,7 @@ __device__ __forceinline__ PairFacts pair_facts(const PlanCtx& c, int p, const C
   f.nb = __ldg(c.B.node_off + pb + 1) - __ldg(c.B.node_off + pb);
   int ea = __ldg(c.A.edge_off + pa + 1) - __ldg(c.A.edge_off + pa);
   int eb = __ldg(c.B.edge_off + pb + 1) - __ldg(c.B.edge_off + pb);
-  Shape s = classify(f.na, f.nb, cc);
+  Shape s = classify(f.na, f.nb, ea, eb, cc);
   f.cls = s.cls;
   // per-iteration work: every entry is written once, every edge pair gathered twice
   f.bucket = cost_bucket((int64_t)f.na * f.nb + 2 * (int64_t)ea * eb);

@@ -212,25 +212,35 @@ def test_device_side_errors_are_reported():
     assert _raw_call(pa, torch.from_numpy(pairs).to(DEV), len(pairs), om, ws) == 0
 
 
-def test_workspace_too_small_for_global_pairs_is_reported():
-    w = config2(30)
-    pa = api.Pack(w.cfgs_a, w.F, device=DEV)
-    pairs = np.ascontiguousarray(w.pairs, np.int32)
-    from paper_1707_02423_gb300 import _binding as Bb
-
-    L = Bb.lib()
-    # the fixed part only: no room for a scratch slot
-    fixed = C.c_size_t(0)
-    # size of the fixed part for P pairs = ws_size of a list without global pairs of the same length
-    ns = np.array([c.n for c in w.cfgs_a])
-    small_pairs = np.full_like(pairs, int(np.argmin(ns)))
-    B.check(L.cf_similarity_ws_size(pa.host_ptr, pa.host_ptr, small_pairs.ctypes.data, len(pairs),
-                                    C.byref(B.params()), C.byref(fixed)))
-    ws = torch.zeros(fixed.value, dtype=torch.uint8, device=DEV)
-    om = torch.ones(w.F, device=DEV)
-    st = _raw_call(pa, torch.from_numpy(pairs).to(DEV), len(pairs), om, ws)
-    big = (ns[pairs[:, 0]] * ns[pairs[:, 1]]).max()
-    assert st == (2 if big > 5632 else 0)
+def test_workspace_slots_for_pairs_beyond_shared_memory():
+    # two 300-block CFGs: their pairs exceed the shared-memory regions and need
+    # scratch slots in the workspace
+    rng = np.random.default_rng(77)
+    cfgs = config2(6).cfgs_a + [structured_cfg(rng, 300, 5, 12), structured_cfg(rng, 290, 5, 12)]
+    pairs = np.array([(6, 7), (0, 6), (7, 6), (1, 2)], np.int32)
+    pa = api.Pack(cfgs, 13, device=DEV)
+    L = B.lib()
+    small = C.c_size_t(0)
+    B.check(L.cf_similarity_ws_size(pa.host_ptr, pa.host_ptr, np.ascontiguousarray(pairs[3:].repeat(4, 0)).ctypes.data,
+                                    4, C.byref(B.params()), C.byref(small)))  # same P, no large pair: fixed part
+    om = torch.ones(13, device=DEV)
+    d_pairs = torch.from_numpy(pairs).to(DEV)
+    ws = torch.zeros(small.value, dtype=torch.uint8, device=DEV)
+    assert _raw_call(pa, d_pairs, len(pairs), om, ws) == 2  # CF_ERR_WORKSPACE: no room for a slot
+    # exactly one slot: the large pairs share it one after another
+    slot = 4 * (3 * 300 * 300 + 2 * 600 + 2 * 300 + 300 + 64)
+    slot = (slot + 255) // 256 * 256
+    ws = torch.zeros(small.value + slot, dtype=torch.uint8, device=DEV)
+    sc = torch.empty(len(pairs), device=DEV)
+    prm = B.params()
+    B.check(L.cf_similarity(pa.dev.data_ptr(), pa.dev.data_ptr(), d_pairs.data_ptr(), len(pairs), C.byref(prm),
+                            om.data_ptr(), None, sc.data_ptr(), None, ws.data_ptr(), ws.numel(), None))
+    assert L.cf_status_check(ws.data_ptr(), None) == 0
+    sc = sc.cpu().numpy()
+    for p, (a, b) in enumerate(pairs):
+        ref = oracle.similarity(cfgs[a], cfgs[b], np.ones(13))["X"]
+        if greedy_margin(ref) > TIE_EPS:
+            assert abs(sc[p] - oracle.greedy_match(ref)[1]) <= ATOL_S
 
 
 def test_match_given_matrices_bit_exact():
