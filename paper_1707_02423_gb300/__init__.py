@@ -10,7 +10,8 @@ from ._binding import CF_NORM_FROB, CF_NORM_NONE, CfsimError, lib  # noqa: F401
 def __getattr__(name):
     # the torch-facing API is imported lazily so that the build step and the
     # CPU-only ABI checks do not need a CUDA device
-    if name in ("Pack", "Workspace", "Result", "similarity", "match", "topk", "out_offsets", "ws_size"):
+    if name in ("Pack", "Workspace", "Result", "similarity", "match", "topk", "out_offsets", "ws_size",
+                "similarity_backward", "CFSimilarity"):
         from . import api
 
         return getattr(api, name)

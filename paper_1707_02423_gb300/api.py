@@ -192,3 +192,64 @@ def topk(scores: torch.Tensor, k: int, stream=None):
     idx = torch.empty(Q, k, dtype=torch.int32, device=s.device)
     B.check(B.lib().cf_topk(s.data_ptr(), Q, Cn, k, top.data_ptr(), idx.data_ptr(), _stream_ptr(stream)))
     return top, idx
+
+
+def backward_ws_size(pa: Pack, pb: Pack, pairs_np: np.ndarray, prm: B.cf_params) -> int:
+    n = C.c_size_t(0)
+    B.check(B.lib().cf_similarity_backward_ws_size(pa.host_ptr, pb.host_ptr, pairs_np.ctypes.data, len(pairs_np),
+                                                   C.byref(prm), C.byref(n)))
+    return n.value
+
+
+def similarity_backward(pa: Pack, pb: Pack, pairs, omega: torch.Tensor, match: torch.Tensor,
+                        grad_scores: torch.Tensor, alpha: float = 0.8, K: int = 40, *,
+                        norm_mode: int = B.CF_NORM_FROB, ws: Workspace | None = None, stream=None):
+    """Gradients of sum_p grad_scores[p] * s_p (cf_similarity_backward) with the
+    matching ``match`` (from the forward) held fixed.
+
+    Returns ``(grad_w_a, grad_w_b, grad_omega)``: user-edge-order gradients of
+    pack A's and pack B's edge weights (``grad_w_b`` is None when both sides
+    are the same pack: everything is in ``grad_w_a``) and of omega."""
+    L = B.lib()
+    pairs_np = _pairs_np(pairs)
+    P = len(pairs_np)
+    dev = pa.dev.device
+    prm = B.params(alpha, K, norm_mode)
+    gwa = torch.zeros(int(pa.info.n_user_edges), dtype=torch.float32, device=dev)
+    gwb = None if pb is pa else torch.zeros(int(pb.info.n_user_edges), dtype=torch.float32, device=dev)
+    gom = torch.zeros(pa.F, dtype=torch.float32, device=dev)
+    ws = ws or Workspace(dev)
+    wbuf = ws.get(backward_ws_size(pa, pb, pairs_np, prm))
+    d_pairs = torch.from_numpy(pairs_np).to(dev)
+    g = grad_scores.detach().to(torch.float32).contiguous()
+    st = _stream_ptr(stream)
+    B.check(L.cf_similarity_backward(pa.dev.data_ptr(), pb.dev.data_ptr(), d_pairs.data_ptr(), P, C.byref(prm),
+                                     omega.detach().contiguous().data_ptr(), match.data_ptr(), g.data_ptr(),
+                                     gwa.data_ptr(), _ptr(gwb), gom.data_ptr(), wbuf.data_ptr(), wbuf.numel(), st))
+    B.check(L.cf_status_check(wbuf.data_ptr(), st))
+    return gwa, gwb, gom
+
+
+class CFSimilarity(torch.autograd.Function):
+    """Graph scores of all pairs as a differentiable function of the edge
+    weights (user edge order) and omega; the matching is held fixed in the
+    backward pass (it is piecewise constant in the inputs).
+
+    ``apply(w_a, w_b, omega, pack_a, pack_b, pairs, alpha, K)``; pass
+    ``w_b = None`` when both sides are the same pack."""
+
+    @staticmethod
+    def forward(ctx, w_a, w_b, omega, pack_a, pack_b, pairs, alpha=0.8, K=40):
+        pack_a.set_weights(w_a)
+        if pack_b is not pack_a:
+            pack_b.set_weights(w_b)
+        res = similarity(pack_a, pack_b, pairs, omega.detach(), alpha, K, want_match=True)
+        ctx.pack_a, ctx.pack_b, ctx.pairs, ctx.alpha, ctx.K = pack_a, pack_b, pairs, alpha, K
+        ctx.save_for_backward(omega.detach(), res.match)
+        return res.scores
+
+    @staticmethod
+    def backward(ctx, g):
+        omega, match = ctx.saved_tensors
+        ga, gb, go = similarity_backward(ctx.pack_a, ctx.pack_b, ctx.pairs, omega, match, g, ctx.alpha, ctx.K)
+        return ga, gb, go, None, None, None, None, None

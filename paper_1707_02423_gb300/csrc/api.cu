@@ -486,23 +486,61 @@ cf_status cf_match(const void* d_pack_a, const void* d_pack_b, const int32_t* d_
 
 cf_status cf_similarity_backward_ws_size(const void* h_pack_a, const void* h_pack_b, const int32_t* h_pairs,
                                          int32_t P, const cf_params* params, size_t* bytes) {
-  (void)h_pack_a;
-  (void)h_pack_b;
-  (void)h_pairs;
-  (void)P;
-  (void)params;
-  (void)bytes;
-  return fail(CF_ERR_UNSUPPORTED, "backward not built yet");
+  if (!bytes) return fail(CF_ERR_INVALID_ARG, "bytes is NULL");
+  cf_status s = check_params(params);
+  if (s) return s;
+  PackHeader ha, hb;
+  s = read_header(h_pack_a, &ha, "h_pack_a");
+  if (s) return s;
+  s = read_header(h_pack_b, &hb, "h_pack_b");
+  if (s) return s;
+  s = scan_pairs(h_pack_a, h_pack_b, h_pairs, P, nullptr, nullptr, nullptr, nullptr);
+  if (s) return s;
+  const int32_t* noa = reinterpret_cast<const int32_t*>(static_cast<const char*>(h_pack_a) + ha.off_node);
+  const int32_t* nob = reinterpret_cast<const int32_t*>(static_cast<const char*>(h_pack_b) + hb.off_node);
+  const int32_t* eoa = reinterpret_cast<const int32_t*>(static_cast<const char*>(h_pack_a) + ha.off_edge);
+  const int32_t* eob = reinterpret_cast<const int32_t*>(static_cast<const char*>(h_pack_b) + hb.off_edge);
+  size_t need = 0;
+  for (int p = 0; p < P; ++p) {
+    const int a = h_pairs[2 * p], b = h_pairs[2 * p + 1];
+    need = std::max(need, bwd_slot_bytes(noa[a + 1] - noa[a], nob[b + 1] - nob[b], eoa[a + 1] - eoa[a],
+                                         eob[b + 1] - eob[b], params->K, ha.F_pad));
+  }
+  const int sms = device_sm_count();
+  const int64_t slots = std::min<int64_t>(P, 2 * (sms > 0 ? sms : 152));
+  // sized as if the two sides were different packs (covers both cases)
+  *bytes = bwd_layout(P, ha.n_edges, hb.n_edges, false).slots + (size_t)slots * need;
+  return ok();
 }
 
 cf_status cf_similarity_backward(const void* d_pack_a, const void* d_pack_b, const int32_t* d_pairs, int32_t P,
                                  const cf_params* params, const float* d_omega, const int32_t* d_match,
                                  const float* d_grad_scores, float* d_grad_w_a, float* d_grad_w_b,
                                  float* d_grad_omega, void* d_ws, size_t ws_bytes, cf_stream_t stream) {
-  (void)d_pack_a, (void)d_pack_b, (void)d_pairs, (void)P, (void)params, (void)d_omega, (void)d_match;
-  (void)d_grad_scores, (void)d_grad_w_a, (void)d_grad_w_b, (void)d_grad_omega, (void)d_ws, (void)ws_bytes;
-  (void)stream;
-  return fail(CF_ERR_UNSUPPORTED, "backward not built yet");
+  cf_status s = check_params(params);
+  if (s) return s;
+  if (params->flags & (CF_FLAG_PER_PAIR_LAUNCH | CF_FLAG_PLAN_ONLY | CF_FLAG_REUSE_PLAN))
+    return fail(CF_ERR_INVALID_ARG, "cf_similarity_backward takes no launch flags");
+  s = check_device_call(d_pack_a, d_pack_b, d_pairs, P, d_ws, ws_bytes);
+  if (s) return s;
+  if (!d_omega || !d_match || !d_grad_scores) return fail(CF_ERR_INVALID_ARG, "d_omega, d_match and d_grad_scores are required");
+  if (d_pack_a == d_pack_b && d_grad_w_b && d_grad_w_b != d_grad_w_a)
+    return fail(CF_ERR_INVALID_ARG, "with one pack on both sides, d_grad_w_b must be NULL or equal d_grad_w_a");
+  if (P == 0) return ok();
+  CallArgs a = base_args(d_pack_a, d_pack_b, d_pairs, P, params, d_omega, d_ws, ws_bytes);
+  a.match_in = d_match;
+  a.grad_scores = d_grad_scores;
+  a.grad_w_a = d_grad_w_a;
+  a.grad_w_b = d_pack_a == d_pack_b ? nullptr : d_grad_w_b;
+  a.grad_omega = d_grad_omega;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(d_ws, 0, sizeof(WsHeader), st);
+  if (e != cudaSuccess) return cuda_fail(e, "workspace reset");
+  e = launch_plan(a, fwd_variant(active_variant()).cc, st);
+  if (e != cudaSuccess) return cuda_fail(e, "plan launch");
+  e = launch_backward(a, st);
+  if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+  return ok();
 }
 
 cf_status cf_topk(const float* d_scores, int32_t Q, int32_t C, int32_t k, float* d_top, int32_t* d_idx,

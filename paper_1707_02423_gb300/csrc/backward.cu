@@ -1,0 +1,467 @@
+// a8: the adjoint of the similarity forward with the matching held fixed:
+// gradients of sum_p g_p s_p with respect to every edge weight of both packs
+// and to the per-feature attribute weights omega.
+//
+// Reverse mode of the forward (Table 1 "Cos" and "Iso" rows, renormalised):
+//   Xbar_K   = g 1[matched entries]
+//   for k = K-1 .. 0:
+//     Ybar     = (Xbar - <Xbar, X_{k+1}> X_{k+1}) / |Y_{k+1}|   (Ybar = Xbar when not renormalised)
+//     Ehatbar += (1 - alpha) Ybar ;  Zbar = alpha Ybar
+//     Wbar_A  += 1/2 (Zbar W_B X_k^T + X_k W_B Zbar^T)  at A's edges
+//     Wbar_B  += 1/2 (Zbar^T W_A X_k + X_k^T W_A Zbar)  at B's edges
+//     Xbar     = 1/2 (W_A^T Zbar W_B + W_A Zbar W_B^T)   (the forward operator: it is self-adjoint)
+//   Ehatbar += Xbar ;  Ebar = (Ehatbar - <Ehatbar, Ehat> Ehat) / |E|
+//   omegabar_f = sum_ij Ebar_ij (a_if b_jf / (r_i c_j) - E_ij (a_if^2 / (2 r_i^2) + b_jf^2 / (2 c_j^2)))
+// An edge p->q of A gets  1/2 sum over B's edges j->v of w_jv (Zbar[p,j] X_k[q,v] + X_k[p,j] Zbar[q,v]),
+// and an edge j->v of B the same terms weighted by w_pq and summed over A's edges.
+//
+// X_k is needed in reverse order: the kernel first recomputes the forward,
+// keeping X every S = ceil(sqrt(K)) steps and every |Y_k|, then walks the
+// segments backwards, recomputing each segment's iterates from its checkpoint
+// (about 2K forward steps and K adjoint steps; S + K/S + 1 matrices resident).
+//
+// One 256-thread CTA per pair, all matrices in a scratch slot of the
+// workspace (L2-resident).  Element loops run a warp per row and the lanes
+// over columns.  An edge's gradient is a warp-reduced sum owned by one warp
+// per step, accumulated in the slot and added to a per-pack distinct-edge
+// array when the pair is done; a last kernel adds those to the caller's
+// user-order buffers.
+#include "device_common.cuh"
+#include "kernels.h"
+
+namespace cfsim {
+
+namespace {
+
+constexpr int kBwdNT = 256;
+constexpr int kBwdWarps = kBwdNT / 32;
+
+__device__ __forceinline__ float block_sum(float v, float* red, int par) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) red[par * 32 + (threadIdx.x >> 5)] = v;
+  __syncthreads();
+  return warp_sum(lane < kBwdWarps ? red[par * 32 + lane] : 0.f);
+}
+
+struct BwdPair {
+  int p, na, nb, ea, eb;
+  const int32_t *ao, *ai, *bo, *bi;  // CFG-local row pointers (global edge indices)
+  const CfAdj *aoa, *aia, *boa, *bia;
+  const float *aat, *bat;  // attribute rows
+  int a_edge0, b_edge0;    // first distinct edge of each CFG in its pack
+};
+
+struct BwdCtx {
+  PackView A, B;
+  const int32_t* pairs;
+  const uint32_t* queue;
+  const int64_t* m_off;
+  const int32_t* match;
+  const float* gbar;
+  float* gcan_a;
+  float* gcan_b;
+  float* gomega;
+  WsHeader* hdr;
+  unsigned char* slots;
+  size_t slots_bytes;
+  const float* om;  // omega, shared-memory copy
+  float alpha;
+  int K, norm_mode, F, Fp;
+  uint32_t n_pairs;  // valid pairs in the queue
+};
+
+// Successor-pair plus predecessor-pair sum of Y at entry (i, j), both graphs'
+// lists read from the pack (A indexes rows, B columns; ld = n_b).
+__device__ __forceinline__ float gather_mem(const float* Y, const BwdPair& q, int i, int j) {
+  float s = 0.f;
+  const int c0 = __ldg(q.bo + j), c1 = __ldg(q.bo + j + 1);
+  for (int e = __ldg(q.ao + i), e1 = __ldg(q.ao + i + 1); e < e1; ++e) {
+    const CfAdj a = ldg_adj(q.aoa + e);
+    const float* row = Y + (size_t)a.nbr * q.nb;
+    float t = 0.f;
+    for (int f = c0; f < c1; ++f) {
+      const CfAdj b = ldg_adj(q.boa + f);
+      t = fmaf(b.w, row[b.nbr], t);
+    }
+    s = fmaf(a.w, t, s);
+  }
+  const int d0 = __ldg(q.bi + j), d1 = __ldg(q.bi + j + 1);
+  for (int e = __ldg(q.ai + i), e1 = __ldg(q.ai + i + 1); e < e1; ++e) {
+    const CfAdj a = ldg_adj(q.aia + e);
+    const float* row = Y + (size_t)a.nbr * q.nb;
+    float t = 0.f;
+    for (int f = d0; f < d1; ++f) {
+      const CfAdj b = ldg_adj(q.bia + f);
+      t = fmaf(b.w, row[b.nbr], t);
+    }
+    s = fmaf(a.w, t, s);
+  }
+  return s;
+}
+
+// One forward step from X (normalised) into Xn:  Y = alpha/2 M(X) + (1-alpha) Ehat,
+// Xn = Y / |Y| (or Y).  Returns |Y| (1 when not renormalised).
+__device__ __forceinline__ float fwd_step(const BwdCtx& cx, const BwdPair& q, const float* X, float* Xn, const float* eh, float* red,
+                          int& par) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const float ca = 0.5f * cx.alpha, cb = 1.f - cx.alpha;
+  float ss = 0.f;
+  for (int i = w; i < q.na; i += kBwdWarps)
+    for (int j = lane; j < q.nb; j += 32) {
+      const size_t o = (size_t)i * q.nb + j;
+      const float y = fmaf(ca, gather_mem(X, q, i, j), cb * eh[o]);
+      Xn[o] = y;
+      ss = fmaf(y, y, ss);
+    }
+  const float yy = block_sum(ss, red, par);
+  par ^= 1;
+  if (cx.norm_mode != 0) return 1.f;
+  const float nY = sqrtf(yy), inv = 1.f / nY;
+  for (int i = w; i < q.na; i += kBwdWarps)
+    for (int j = lane; j < q.nb; j += 32) Xn[(size_t)i * q.nb + j] *= inv;
+  __syncthreads();
+  return nY;
+}
+
+__device__ __forceinline__ void run_pair_bwd(const BwdCtx& cx, const BwdPair& q, float* slot, float* red) {
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int na = q.na, nb = q.nb;
+  const size_t E = (size_t)na * nb;
+  const int K = cx.K, S = bwd_segment(K), nck = K / S + 1;
+  // slot layout (bwd_slot_bytes)
+  float* er = slot;                        // E (raw cosine term)
+  float* eh = er + E;                      // Ehat
+  float* ehb = eh + E;                     // Ehat-bar, then E-bar
+  float* xb = ehb + E;                     // X-bar
+  float* zb = xb + E;                      // Z-bar
+  float* ck = zb + E;                      // checkpoints [nck][E]
+  float* sg = ck + (size_t)nck * E;        // one segment's iterates [S + 1][E]
+  float* nrm = sg + (size_t)(S + 1) * E;   // |Y_k|, k = 0..K
+  float* rn = nrm + (K + 2);               // weighted attribute norms of A's blocks
+  float* cn = rn + na;                     //   and of B's blocks
+  float* rho = cn + nb;                    // sum_j Ebar_ij E_ij
+  float* gam = rho + na;                   // sum_i Ebar_ij E_ij
+  int* asrc = reinterpret_cast<int*>(gam + nb);
+  int* adst = asrc + q.ea;
+  float* aw = reinterpret_cast<float*>(adst + q.ea);
+  float* ga = aw + q.ea;
+  int* bsrc = reinterpret_cast<int*>(ga + q.ea);
+  int* bdst = bsrc + q.eb;
+  float* bw = reinterpret_cast<float*>(bdst + q.eb);
+  float* gb = bw + q.eb;
+  float* Rf = gb + q.eb;  // [na][Fp]: sum_j Ebar_ij b_jf / c_j
+  int par = 0;
+
+  // both graphs' edge lists (CFG-local distinct-edge order), zeroed accumulators
+  for (int i = t; i < na; i += kBwdNT)
+    for (int e = __ldg(q.ao + i), e1 = __ldg(q.ao + i + 1); e < e1; ++e) {
+      const CfAdj a = ldg_adj(q.aoa + e);
+      const int l = e - q.a_edge0;
+      asrc[l] = i;
+      adst[l] = a.nbr;
+      aw[l] = a.w;
+      ga[l] = 0.f;
+    }
+  for (int j = t; j < nb; j += kBwdNT)
+    for (int e = __ldg(q.bo + j), e1 = __ldg(q.bo + j + 1); e < e1; ++e) {
+      const CfAdj b = ldg_adj(q.boa + e);
+      const int l = e - q.b_edge0;
+      bsrc[l] = j;
+      bdst[l] = b.nbr;
+      bw[l] = b.w;
+      gb[l] = 0.f;
+    }
+  // E, |E|, Ehat = X_0 (checkpoint 0)
+  for (int i = t; i < na; i += kBwdNT) rn[i] = attr_norm(q.aat + (size_t)i * cx.Fp, cx.om, cx.Fp);
+  for (int j = t; j < nb; j += kBwdNT) cn[j] = attr_norm(q.bat + (size_t)j * cx.Fp, cx.om, cx.Fp);
+  __syncthreads();
+  float ss = 0.f;
+  for (int i = w; i < na; i += kBwdWarps)
+    for (int j = lane; j < nb; j += 32) {
+      const float dot = attr_dot(q.aat + (size_t)i * cx.Fp, q.bat + (size_t)j * cx.Fp, cx.om, cx.Fp);
+      const float den = rn[i] * cn[j];
+      const float e = den > 0.f ? dot / den : 0.f;
+      er[(size_t)i * nb + j] = e;
+      ss = fmaf(e, e, ss);
+    }
+  const float nE = sqrtf(block_sum(ss, red, par));
+  par ^= 1;
+  const float inv = nE > 0.f ? 1.f / nE : 0.f;
+  const float uni = 1.f / sqrtf((float)na * (float)nb);
+  for (int i = w; i < na; i += kBwdWarps)
+    for (int j = lane; j < nb; j += 32) {
+      const size_t o = (size_t)i * nb + j;
+      const float v = nE > 0.f ? er[o] * inv : uni;
+      eh[o] = v;
+      ck[o] = v;
+    }
+  if (t == 0) nrm[0] = 1.f;
+  __syncthreads();
+
+  // forward, keeping X every S steps
+  const float* X = ck;
+  for (int k = 0; k < K; ++k) {
+    float* dst = ((k + 1) % S == 0) ? ck + (size_t)((k + 1) / S) * E : sg + (size_t)((k + 1) % S) * E;
+    const float nY = fwd_step(cx, q, X, dst, eh, red, par);
+    if (t == 0) nrm[k + 1] = nY;
+    X = dst;
+  }
+  // Xbar_K = g 1[matched], Ehatbar = 0
+  for (int i = w; i < na; i += kBwdWarps)
+    for (int j = lane; j < nb; j += 32) {
+      const size_t o = (size_t)i * nb + j;
+      xb[o] = 0.f;
+      ehb[o] = 0.f;
+    }
+  __syncthreads();
+  const float g = cx.gbar[q.p];
+  for (int i = t; i < na; i += kBwdNT) {
+    const int m = cx.match[cx.m_off[q.p] + i];
+    if (m >= 0 && m < nb) xb[(size_t)i * nb + m] = g;
+  }
+  __syncthreads();
+
+  // adjoint sweep, one segment at a time from the last
+  for (int seg = (K - 1) / S; seg >= 0 && K > 0; --seg) {
+    const int k0 = seg * S, k1 = min(K, k0 + S);
+    for (int i = w; i < na; i += kBwdWarps)
+      for (int j = lane; j < nb; j += 32) sg[(size_t)i * nb + j] = ck[(size_t)seg * E + (size_t)i * nb + j];
+    __syncthreads();
+    for (int k = k0; k < k1 - 1; ++k) fwd_step(cx, q, sg + (size_t)(k - k0) * E, sg + (size_t)(k - k0 + 1) * E, eh, red, par);
+    // the segment's last iterate X_{k1} is the next checkpoint (or X_K)
+    const float* Xend = (k1 % S == 0) ? ck + (size_t)(k1 / S) * E : sg + (size_t)(k1 - k0) * E;
+    if (k1 % S != 0) fwd_step(cx, q, sg + (size_t)(k1 - 1 - k0) * E, sg + (size_t)(k1 - k0) * E, eh, red, par);
+    for (int k = k1 - 1; k >= k0; --k) {
+      const float* X1 = (k + 1 == k1) ? Xend : sg + (size_t)(k + 1 - k0) * E;
+      const float* Xk = sg + (size_t)(k - k0) * E;
+      float d = 0.f;
+      if (cx.norm_mode == 0) {
+        float acc = 0.f;
+        for (int i = w; i < na; i += kBwdWarps)
+          for (int j = lane; j < nb; j += 32) acc = fmaf(xb[(size_t)i * nb + j], X1[(size_t)i * nb + j], acc);
+        d = block_sum(acc, red, par);
+        par ^= 1;
+      }
+      const float invY = cx.norm_mode == 0 ? 1.f / nrm[k + 1] : 1.f;
+      for (int i = w; i < na; i += kBwdWarps)
+        for (int j = lane; j < nb; j += 32) {
+          const size_t o = (size_t)i * nb + j;
+          const float yb = (xb[o] - d * X1[o]) * invY;
+          ehb[o] = fmaf(1.f - cx.alpha, yb, ehb[o]);
+          zb[o] = cx.alpha * yb;
+        }
+      __syncthreads();
+      // edge gradients at this step
+      for (int e = w; e < q.ea; e += kBwdWarps) {
+        const int p = asrc[e], qq = adst[e];
+        float s = 0.f;
+        for (int f = lane; f < q.eb; f += 32) {
+          const int j = bsrc[f], v = bdst[f];
+          const float T = fmaf(zb[(size_t)p * nb + j], Xk[(size_t)qq * nb + v], Xk[(size_t)p * nb + j] * zb[(size_t)qq * nb + v]);
+          s = fmaf(bw[f], T, s);
+        }
+        s = warp_sum(s);
+        if (lane == 0) ga[e] = fmaf(0.5f, s, ga[e]);
+      }
+      for (int f = w; f < q.eb; f += kBwdWarps) {
+        const int j = bsrc[f], v = bdst[f];
+        float s = 0.f;
+        for (int e = lane; e < q.ea; e += 32) {
+          const int p = asrc[e], qq = adst[e];
+          const float T = fmaf(zb[(size_t)p * nb + j], Xk[(size_t)qq * nb + v], Xk[(size_t)p * nb + j] * zb[(size_t)qq * nb + v]);
+          s = fmaf(aw[e], T, s);
+        }
+        s = warp_sum(s);
+        if (lane == 0) gb[f] = fmaf(0.5f, s, gb[f]);
+      }
+      // Xbar_k = 1/2 M(Zbar)
+      for (int i = w; i < na; i += kBwdWarps)
+        for (int j = lane; j < nb; j += 32) xb[(size_t)i * nb + j] = 0.5f * gather_mem(zb, q, i, j);
+      __syncthreads();
+    }
+  }
+  // Ehatbar += Xbar_0
+  for (int i = w; i < na; i += kBwdWarps)
+    for (int j = lane; j < nb; j += 32) ehb[(size_t)i * nb + j] += xb[(size_t)i * nb + j];
+  __syncthreads();
+
+  // omega gradient through the cosine term (rows / columns with a zero norm have E = 0 and no gradient)
+  if (cx.gomega && nE > 0.f) {
+    float acc = 0.f;
+    for (int i = w; i < na; i += kBwdWarps)
+      for (int j = lane; j < nb; j += 32) acc = fmaf(ehb[(size_t)i * nb + j], eh[(size_t)i * nb + j], acc);
+    const float d = block_sum(acc, red, par);
+    par ^= 1;
+    for (int i = w; i < na; i += kBwdWarps)
+      for (int j = lane; j < nb; j += 32) {
+        const size_t o = (size_t)i * nb + j;
+        ehb[o] = (ehb[o] - d * eh[o]) / nE;  // Ebar
+      }
+    __syncthreads();
+    for (int i = w; i < na; i += kBwdWarps) {
+      float r = 0.f;
+      for (int j = lane; j < nb; j += 32) r = fmaf(ehb[(size_t)i * nb + j], er[(size_t)i * nb + j], r);
+      r = warp_sum(r);
+      if (lane == 0) rho[i] = r;
+      for (int f = 0; f < cx.F; ++f) {
+        float s = 0.f;
+        for (int j = lane; j < nb; j += 32)
+          if (cn[j] > 0.f) s = fmaf(ehb[(size_t)i * nb + j], __ldg(q.bat + (size_t)j * cx.Fp + f) / cn[j], s);
+        s = warp_sum(s);
+        if (lane == 0) Rf[(size_t)i * cx.Fp + f] = s;
+      }
+    }
+    for (int j = w; j < nb; j += kBwdWarps) {
+      float s = 0.f;
+      for (int i = lane; i < na; i += 32) s = fmaf(ehb[(size_t)i * nb + j], er[(size_t)i * nb + j], s);
+      s = warp_sum(s);
+      if (lane == 0) gam[j] = s;
+    }
+    __syncthreads();
+    for (int f = t; f < cx.F; f += kBwdNT) {
+      float g1 = 0.f, g2 = 0.f, g3 = 0.f;
+      for (int i = 0; i < na; ++i)
+        if (rn[i] > 0.f) {
+          const float a = __ldg(q.aat + (size_t)i * cx.Fp + f);
+          g1 = fmaf(a / rn[i], Rf[(size_t)i * cx.Fp + f], g1);
+          g2 = fmaf(a * a / (2.f * rn[i] * rn[i]), rho[i], g2);
+        }
+      for (int j = 0; j < nb; ++j)
+        if (cn[j] > 0.f) {
+          const float b = __ldg(q.bat + (size_t)j * cx.Fp + f);
+          g3 = fmaf(b * b / (2.f * cn[j] * cn[j]), gam[j], g3);
+        }
+      atomicAdd(cx.gomega + f, g1 - g2 - g3);
+    }
+  }
+  // this pair's edge gradients into the packs' distinct-edge accumulators
+  for (int e = t; e < q.ea; e += kBwdNT) atomicAdd(cx.gcan_a + q.a_edge0 + e, ga[e]);
+  for (int f = t; f < q.eb; f += kBwdNT) atomicAdd(cx.gcan_b + q.b_edge0 + f, gb[f]);
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBwdNT, 1) bwd_kernel(CallArgs a) {
+  __shared__ __align__(16) float s_om[kMaxF];
+  __shared__ float s_red[64];
+  __shared__ BwdCtx s_cx;
+  __shared__ uint32_t s_q;
+  if (threadIdx.x == 0) {
+    BwdCtx& c = s_cx;
+    c.A = load_pack(a.pack_a);
+    c.B = load_pack(a.pack_b);
+    const WsLayout L = ws_layout(a.P);
+    c.hdr = reinterpret_cast<WsHeader*>(a.ws + L.hdr);
+    c.queue = reinterpret_cast<const uint32_t*>(a.ws + L.queue);
+    c.m_off = reinterpret_cast<const int64_t*>(a.ws + L.m_off);
+    const PackHeader* ha = reinterpret_cast<const PackHeader*>(a.pack_a);
+    const PackHeader* hb = reinterpret_cast<const PackHeader*>(a.pack_b);
+    const BwdLayout B = bwd_layout(a.P, ha->n_edges, hb->n_edges, a.pack_a == a.pack_b);
+    c.gcan_a = reinterpret_cast<float*>(a.ws + B.grad_a);
+    c.gcan_b = reinterpret_cast<float*>(a.ws + B.grad_b);
+    c.slots = a.ws + B.slots;
+    c.slots_bytes = a.ws_bytes > B.slots ? a.ws_bytes - B.slots : 0;
+    c.pairs = a.pairs;
+    c.match = a.match_in;
+    c.gbar = a.grad_scores;
+    c.gomega = a.grad_omega;
+    c.alpha = a.alpha;
+    c.K = a.K;
+    c.norm_mode = a.norm_mode;
+    c.F = c.A.F;
+    c.Fp = c.A.F_pad;
+    c.om = s_om;
+    uint32_t n = 0;
+    for (int k = 0; k < kNumClasses; ++k) n += c.hdr->n_class[k];
+    c.n_pairs = n;
+  }
+  __syncthreads();
+  const BwdCtx& cx = s_cx;
+  if (threadIdx.x < kMaxF) s_om[threadIdx.x] = threadIdx.x < cx.F ? a.omega[threadIdx.x] : 0.f;
+  __syncthreads();
+  const uint64_t need = cx.hdr->bwd_slot_need;
+  const uint64_t nslots = need ? cx.slots_bytes / need : 0;
+  if (nslots == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && cx.n_pairs > 0) set_status(cx.hdr, 2 /* CF_ERR_WORKSPACE */, -1);
+    return;
+  }
+  if (blockIdx.x >= nslots) return;
+  float* slot = reinterpret_cast<float*>(cx.slots + (size_t)blockIdx.x * need);
+  for (;;) {
+    if (threadIdx.x == 0) s_q = atomicAdd(&cx.hdr->q_bwd, 1u);
+    __syncthreads();
+    const uint32_t qi = s_q;
+    __syncthreads();
+    if (qi >= cx.n_pairs) break;
+    BwdPair q;
+    q.p = (int)cx.queue[qi];
+    const int pa = cx.pairs[2 * q.p], pb = cx.pairs[2 * q.p + 1];
+    const int ba = cx.A.node_off[pa], bb = cx.B.node_off[pb];
+    q.na = cx.A.node_off[pa + 1] - ba;
+    q.nb = cx.B.node_off[pb + 1] - bb;
+    q.a_edge0 = cx.A.edge_off[pa];
+    q.b_edge0 = cx.B.edge_off[pb];
+    q.ea = cx.A.edge_off[pa + 1] - q.a_edge0;
+    q.eb = cx.B.edge_off[pb + 1] - q.b_edge0;
+    q.ao = cx.A.out_ptr + ba;
+    q.ai = cx.A.in_ptr + ba;
+    q.bo = cx.B.out_ptr + bb;
+    q.bi = cx.B.in_ptr + bb;
+    q.aoa = cx.A.out_adj;
+    q.aia = cx.A.in_adj;
+    q.boa = cx.B.out_adj;
+    q.bia = cx.B.in_adj;
+    q.aat = cx.A.attr + (size_t)ba * cx.Fp;
+    q.bat = cx.B.attr + (size_t)bb * cx.Fp;
+    run_pair_bwd(cx, q, slot, s_red);
+  }
+}
+
+// Zero the distinct-edge accumulators (sizes read from the pack headers).
+__global__ void bwd_zero_kernel(CallArgs a) {
+  const PackHeader* ha = reinterpret_cast<const PackHeader*>(a.pack_a);
+  const PackHeader* hb = reinterpret_cast<const PackHeader*>(a.pack_b);
+  const bool same = a.pack_a == a.pack_b;
+  const BwdLayout B = bwd_layout(a.P, ha->n_edges, hb->n_edges, same);
+  float* ga = reinterpret_cast<float*>(a.ws + B.grad_a);
+  float* gb = reinterpret_cast<float*>(a.ws + B.grad_b);
+  const int64_t n = ha->n_edges + (same ? 0 : hb->n_edges);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    (k < ha->n_edges ? ga[k] : gb[k - ha->n_edges]) = 0.f;
+}
+
+// out[e] += the distinct-edge gradient of user edge e, for every user edge.
+__global__ void bwd_scatter_kernel(CallArgs a, int side) {
+  const void* pack = side == 0 ? a.pack_a : a.pack_b;
+  const PackHeader* ha = reinterpret_cast<const PackHeader*>(a.pack_a);
+  const PackHeader* hb = reinterpret_cast<const PackHeader*>(a.pack_b);
+  const BwdLayout B = bwd_layout(a.P, ha->n_edges, hb->n_edges, a.pack_a == a.pack_b);
+  const float* g = reinterpret_cast<const float*>(a.ws + (side == 0 ? B.grad_a : B.grad_b));
+  const PackView v = load_pack(pack);
+  const int64_t n = reinterpret_cast<const PackHeader*>(pack)->n_user_edges;
+  float* out = side == 0 ? a.grad_w_a : a.grad_w_b;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] += g[v.u2c[e]];
+}
+
+int g_bwd_sm = 0;
+
+}  // namespace
+
+cudaError_t launch_backward(const CallArgs& a, cudaStream_t s) {
+  if (g_bwd_sm == 0) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&g_bwd_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+  bwd_zero_kernel<<<2 * g_bwd_sm, 256, 0, s>>>(a);
+  const int grid = a.P < 2 * g_bwd_sm ? a.P : 2 * g_bwd_sm;
+  bwd_kernel<<<grid, kBwdNT, 0, s>>>(a);
+  if (a.grad_w_a) bwd_scatter_kernel<<<2 * g_bwd_sm, 256, 0, s>>>(a, 0);
+  if (a.grad_w_b && a.pack_a != a.pack_b) bwd_scatter_kernel<<<2 * g_bwd_sm, 256, 0, s>>>(a, 1);
+  return cudaGetLastError();
+}
+
+}  // namespace cfsim

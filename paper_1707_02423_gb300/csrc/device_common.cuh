@@ -1,5 +1,5 @@
 // Device helpers shared by the kernels: resolved pack views, status word,
-// warp/CTA reductions and the two thread-group shapes a pair runs on.
+// warp reductions, named barriers and the weighted attribute products.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -83,55 +83,39 @@ __device__ __forceinline__ void warp_argmax(float& v, int& i) {
   }
 }
 
-// A warp working on one pair on its own.
-struct WarpGrp {
-  int lane;
-  __device__ __forceinline__ int rank() const { return lane; }
-  static constexpr int size() { return 32; }
-  __device__ __forceinline__ int warp() const { return 0; }
-  static constexpr int nwarps() { return 1; }
-  __device__ __forceinline__ void sync() const { __syncwarp(); }
-  // Sum over the group; every thread gets the same value.  `red`/`par` unused.
-  __device__ __forceinline__ float sum(float v, float*, int) const {
-    v = warp_sum(v);
-    __syncwarp();
-    return v;
-  }
-  __device__ __forceinline__ int sum_i(int v, int*, int) const {
-    v = warp_sum_i(v);
-    __syncwarp();
-    return v;
-  }
-};
+__device__ __forceinline__ void bar_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
 
-// A whole CTA working on one pair.  sum() contains the group's one barrier;
-// `red` holds two parities of per-warp partials so that consecutive sums
-// need no second barrier.
-template <int NT>
-struct CtaGrp {
-  __device__ __forceinline__ int rank() const { return threadIdx.x; }
-  static constexpr int size() { return NT; }
-  __device__ __forceinline__ int warp() const { return threadIdx.x >> 5; }
-  static constexpr int nwarps() { return NT / 32; }
-  __device__ __forceinline__ void sync() const { __syncthreads(); }
-  __device__ __forceinline__ float sum(float v, float* red, int par) const {
-    v = warp_sum(v);
-    if ((threadIdx.x & 31) == 0) red[par * 32 + (threadIdx.x >> 5)] = v;
-    __syncthreads();
-    float t = 0.f;
-#pragma unroll
-    for (int w = 0; w < NT / 32; ++w) t += red[par * 32 + w];
-    return t;
+// Weighted attribute norm sqrt(sum_f w_f a_f^2) and weighted dot product
+// sum_f w_f a_f b_f over the zero-padded F_pad columns, four at a time.
+__device__ __forceinline__ float attr_norm(const float* a, const float* om, int Fp) {
+  const float4* a4 = reinterpret_cast<const float4*>(a);
+  const float4* o4 = reinterpret_cast<const float4*>(om);
+  float acc = 0.f;
+  for (int q = 0; q < (Fp >> 2); ++q) {
+    const float4 v = __ldg(a4 + q), w = o4[q];
+    acc = fmaf(w.x * v.x, v.x, acc);
+    acc = fmaf(w.y * v.y, v.y, acc);
+    acc = fmaf(w.z * v.z, v.z, acc);
+    acc = fmaf(w.w * v.w, v.w, acc);
   }
-  __device__ __forceinline__ int sum_i(int v, int* red, int par) const {
-    v = warp_sum_i(v);
-    if ((threadIdx.x & 31) == 0) red[par * 32 + (threadIdx.x >> 5)] = v;
-    __syncthreads();
-    int t = 0;
-#pragma unroll
-    for (int w = 0; w < NT / 32; ++w) t += red[par * 32 + w];
-    return t;
+  return sqrtf(acc);
+}
+
+__device__ __forceinline__ float attr_dot(const float* a, const float* b, const float* om, int Fp) {
+  const float4* a4 = reinterpret_cast<const float4*>(a);
+  const float4* b4 = reinterpret_cast<const float4*>(b);
+  const float4* o4 = reinterpret_cast<const float4*>(om);
+  float acc = 0.f;
+  for (int q = 0; q < (Fp >> 2); ++q) {
+    const float4 u = __ldg(a4 + q), v = __ldg(b4 + q), w = o4[q];
+    acc = fmaf(w.x * u.x, v.x, acc);
+    acc = fmaf(w.y * u.y, v.y, acc);
+    acc = fmaf(w.z * u.z, v.z, acc);
+    acc = fmaf(w.w * u.w, v.w, acc);
   }
-};
+  return acc;
+}
 
 }  // namespace cfsim

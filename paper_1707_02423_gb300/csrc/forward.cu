@@ -92,10 +92,6 @@ __device__ __forceinline__ Geo make_geo(const Ctx& cx, int p, const ClassCfg& cc
   return g;
 }
 
-__device__ __forceinline__ void bar_sync(int id, int nthreads) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
 // A group of threads working on one pair: a single warp (bar < 0) or a set of
 // whole warps synchronised by named barrier `bar`.  sum() contains the
 // group's one barrier; `redf`/`redi` hold two parities of per-warp partials
@@ -266,37 +262,6 @@ __device__ __forceinline__ float gather_g(const float* Y, int ld, const Geo& g, 
     s = fmaf(a.w, t, s);
   }
   return s;
-}
-
-// Weighted attribute norm sqrt(sum_f w_f a_f^2) and weighted dot product
-// sum_f w_f a_f b_f over the zero-padded F_pad columns, four at a time.
-__device__ __forceinline__ float attr_norm(const float* a, const float* om, int Fp) {
-  const float4* a4 = reinterpret_cast<const float4*>(a);
-  const float4* o4 = reinterpret_cast<const float4*>(om);
-  float acc = 0.f;
-  for (int q = 0; q < (Fp >> 2); ++q) {
-    const float4 v = __ldg(a4 + q), w = o4[q];
-    acc = fmaf(w.x * v.x, v.x, acc);
-    acc = fmaf(w.y * v.y, v.y, acc);
-    acc = fmaf(w.z * v.z, v.z, acc);
-    acc = fmaf(w.w * v.w, v.w, acc);
-  }
-  return sqrtf(acc);
-}
-
-__device__ __forceinline__ float attr_dot(const float* a, const float* b, const float* om, int Fp) {
-  const float4* a4 = reinterpret_cast<const float4*>(a);
-  const float4* b4 = reinterpret_cast<const float4*>(b);
-  const float4* o4 = reinterpret_cast<const float4*>(om);
-  float acc = 0.f;
-  for (int q = 0; q < (Fp >> 2); ++q) {
-    const float4 u = __ldg(a4 + q), v = __ldg(b4 + q), w = o4[q];
-    acc = fmaf(w.x * u.x, v.x, acc);
-    acc = fmaf(w.y * u.y, v.y, acc);
-    acc = fmaf(w.z * u.z, v.z, acc);
-    acc = fmaf(w.w * u.w, v.w, acc);
-  }
-  return acc;
 }
 
 // a5-a6: greedy matching by rounds of locally dominant entries, and the score.

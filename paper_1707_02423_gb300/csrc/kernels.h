@@ -55,6 +55,9 @@ cudaError_t launch_match_only(const CallArgs& a, cudaStream_t s);
 cudaError_t launch_set_weights(CfAdj* out_adj, CfAdj* in_adj, const int32_t* in_eid, const int32_t* u2c,
                                int64_t n_user_edges, int64_t n_edges, const float* w_user, cudaStream_t s);
 
+// a8: adjoint (workspace layout bwd_layout; the plan must have run).
+cudaError_t launch_backward(const CallArgs& a, cudaStream_t s);
+
 // Top-k per row.
 cudaError_t launch_topk(const float* scores, int Q, int C, int k, float* top, int32_t* idx, cudaStream_t s);
 

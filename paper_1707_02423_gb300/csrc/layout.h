@@ -147,6 +147,28 @@ CF_HD size_t global_slot_bytes(int na, int nb) {
   return align_up(4 * (3 * e + 2 * (size_t)(na + nb) + 2 * (size_t)na + nb + 64), kAlign);
 }
 
+// Adjoint checkpoints: X_k is kept for k = 0, S, 2S, ... with S = ceil(sqrt(K)),
+// and each segment of S steps is recomputed from its checkpoint.
+CF_HD int bwd_segment(int K) {
+  int s = 1;
+  while (s * s < K) ++s;
+  return s;
+}
+
+// Adjoint scratch of one pair (n_a x n_b matrices, row-major, stride n_b):
+// E, Ehat, Ehat-bar, X-bar, Z-bar, the checkpoints and one segment of
+// iterates; the squared-norm history; attribute norms; both graphs' edge lists
+// (source, target, weight) and their gradient accumulators; per-row
+// projections for the omega gradient.
+CF_HD size_t bwd_slot_bytes(int na, int nb, int ea, int eb, int K, int Fp) {
+  const size_t E = (size_t)na * nb;
+  const int S = bwd_segment(K);
+  const int nck = K / S + 1;
+  const size_t floats = E * (5 + (size_t)nck + (size_t)S + 1) + (size_t)(K + 2) + 2 * (size_t)(na + nb) +
+                        4 * (size_t)(ea + eb) + (size_t)na * Fp + 64;
+  return align_up(4 * floats, kAlign);
+}
+
 // Cost bucket: two buckets per octave of the per-iteration work.
 CF_HD int cost_bucket(int64_t cost) {
   int b = 0;
@@ -165,7 +187,10 @@ struct WsHeader {
   int32_t status_info;  // pair index or other detail of that error
   uint32_t q_next[kNumClasses];
   uint32_t n_class[kNumClasses];
-  uint64_t slot_need;  // bytes of scratch the largest global-class pair needs
+  uint64_t slot_need;      // bytes of scratch the largest global-class pair needs
+  uint64_t bwd_slot_need;  // bytes of adjoint scratch the largest pair needs
+  uint32_t q_bwd;          // adjoint work counter
+  uint32_t pad_;
   uint32_t hist[kNumClasses][kBuckets];
   uint32_t cursor[kNumClasses][kBuckets];
   int64_t x_total, m_total;
@@ -196,6 +221,23 @@ CF_HD WsLayout ws_layout(int P) {
   L.scratch = o;
   L.fixed_bytes = o;
   return L;
+}
+
+// Adjoint workspace: the forward's fixed part, one float per distinct edge of
+// pack A and (unless both sides are the same pack) of pack B, then the slots.
+struct BwdLayout {
+  size_t grad_a, grad_b, slots;
+};
+
+CF_HD BwdLayout bwd_layout(int P, int64_t ne_a, int64_t ne_b, bool same) {
+  BwdLayout B{};
+  size_t o = ws_layout(P).fixed_bytes;
+  B.grad_a = o;
+  o = align_up(o + 4 * (size_t)(ne_a > 0 ? ne_a : 1), kAlign);
+  B.grad_b = same ? B.grad_a : o;
+  if (!same) o = align_up(o + 4 * (size_t)(ne_b > 0 ? ne_b : 1), kAlign);
+  B.slots = o;
+  return B;
 }
 
 }  // namespace cfsim

@@ -44,7 +44,7 @@ __device__ __forceinline__ PlanCtx plan_ctx(const CallArgs& a) {
 
 struct PairFacts {
   bool valid;
-  int na, nb;
+  int na, nb, ea, eb;
   int cls, bucket;
 };
 
@@ -58,8 +58,10 @@ __device__ __forceinline__ PairFacts pair_facts(const PlanCtx& c, int p, const C
   }
   f.na = __ldg(c.A.node_off + pa + 1) - __ldg(c.A.node_off + pa);
   f.nb = __ldg(c.B.node_off + pb + 1) - __ldg(c.B.node_off + pb);
-  int ea = __ldg(c.A.edge_off + pa + 1) - __ldg(c.A.edge_off + pa);
-  int eb = __ldg(c.B.edge_off + pb + 1) - __ldg(c.B.edge_off + pb);
+  const int ea = __ldg(c.A.edge_off + pa + 1) - __ldg(c.A.edge_off + pa);
+  const int eb = __ldg(c.B.edge_off + pb + 1) - __ldg(c.B.edge_off + pb);
+  f.ea = ea;
+  f.eb = eb;
   Shape s = classify(f.na, f.nb, ea, eb, cc);
   f.cls = s.cls;
   // per-iteration work: every entry is written once, every edge pair gathered twice
@@ -116,6 +118,8 @@ __global__ void __launch_bounds__(kPlanThreads) plan_count_kernel(CallArgs a, Cl
       if (f.cls == kClassGlobal)
         atomicMax(reinterpret_cast<unsigned long long*>(&c.hdr->slot_need),
                   (unsigned long long)global_slot_bytes(f.na, f.nb));
+      atomicMax(reinterpret_cast<unsigned long long*>(&c.hdr->bwd_slot_need),
+                (unsigned long long)bwd_slot_bytes(f.na, f.nb, f.ea, f.eb, a.K, c.A.F_pad));
       xc = (int64_t)f.na * f.nb;
       mc = f.na;
     }
