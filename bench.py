@@ -37,14 +37,23 @@ sys.path.insert(0, ROOT)
 METRIC = "CFG-pair similarity evals/sec (fwd, fwd+bwd) batched vs per-pair, % roofline"
 UNIT = "pairs/s"
 ALPHA, K_ITERS = 0.8, 40
-WORKLOAD = ("cfg2: all 19,900 pairs of 200 seeded CFGs, n log-uniform 8-120, depth<=5, F=13 "
-            "(12 instruction categories + registers), K=40, alpha=0.8, greedy matching + score")
+WORKLOADS = {
+    "cfg2": "cfg2: all 19,900 pairs of 200 seeded CFGs, n log-uniform 8-120, depth<=5, F=13 "
+            "(12 instruction categories + registers), K=40, alpha=0.8, greedy matching + score",
+    "cfg3": "cfg3: all 2,016 pairs of 64 seeded CFGs, n 500-2000, loops unrolled 4-16x, F=13 "
+            "(12 categories + block frequency), K=40, greedy matching + score",
+    "cfg4": "cfg4: 256 seeded pairs, n log-uniform 10-300, F=13, K=40: forward (scores + matchings) "
+            "and the adjoint (edge-weight and omega gradients, sqrt(K) checkpoints)",
+    "cfg5": "cfg5: 32 query CFGs x 10,000-CFG corpus (320,000 pairs), n log-uniform 5-400, F=25, K=40: "
+            "scores, top-16 per query, then matchings of the 512 winners",
+}
+WORKLOAD = WORKLOADS["cfg2"]
 
 
-def workload():
-    from gen import config2
+def workload(name="cfg2"):
+    from gen import config2, config3, config4, config5
 
-    return config2()
+    return {"cfg2": config2, "cfg3": config3, "cfg4": config4, "cfg5": config5}[name]()
 
 
 def algorithmic(w, K):
@@ -214,6 +223,107 @@ def run_reference(args):
     }), flush=True)
 
 
+def timed_steps(step, steps, warmup, flush, stream):
+    """Per-step CUDA-event times (ms) of `step`, L2 flushed before each step
+    outside the events."""
+    import torch
+
+    for _ in range(warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in ev:
+        flush.zero_()
+        e0.record(stream)
+        step()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return [e0.elapsed_time(e1) for e0, e1 in ev]
+
+
+def make_step(name, dev):
+    """The step of one workload through the Python API: returns (step, n_pairs,
+    launches_per_step)."""
+    import torch
+
+    from paper_1707_02423_gb300 import _binding as B
+    from paper_1707_02423_gb300 import api
+
+    w = workload(name)
+    pairs_np = np.ascontiguousarray(w.pairs, np.int32)
+    P = len(pairs_np)
+    pa = api.Pack(w.cfgs_a, w.F, device=dev)
+    pb = pa if w.shared else api.Pack(w.cfgs_b, w.F, device=dev)
+    omega = torch.ones(w.F, dtype=torch.float32, device=dev)
+    d_pairs = torch.from_numpy(pairs_np).to(dev)
+    ws = api.Workspace(dev)
+    prm = B.params(ALPHA, K_ITERS)
+    x_off, m_off = api.out_offsets(pa, pb, pairs_np)
+    out = {"scores": torch.empty(P, dtype=torch.float32, device=dev),
+           "match": torch.empty(int(m_off[-1]), dtype=torch.int32, device=dev)}
+    if name in ("cfg2", "cfg3"):
+        ws_bytes = api.ws_size(pa, pb, pairs_np, prm)
+
+        def step():
+            api.similarity(pa, pb, pairs_np, omega, ALPHA, K_ITERS, want_match=True, ws=ws, d_pairs=d_pairs,
+                           out=out, check_status=False, ws_bytes=ws_bytes)
+        return step, P, 4
+    if name == "cfg4":
+        ws_bytes = api.ws_size(pa, pb, pairs_np, prm)
+        bws = api.Workspace(dev)
+        g = torch.ones(P, dtype=torch.float32, device=dev)
+
+        def step():
+            api.similarity(pa, pb, pairs_np, omega, ALPHA, K_ITERS, want_match=True, ws=ws, d_pairs=d_pairs,
+                           out=out, check_status=False, ws_bytes=ws_bytes)
+            api.similarity_backward(pa, pb, pairs_np, omega, out["match"], g, ALPHA, K_ITERS, ws=bws)
+        return step, P, 4 + 7
+    # cfg5: scores of every query-corpus pair, top-16 per query, matchings of the winners
+    nq, nc, k = w.meta["n_query"], w.meta["n_corpus"], w.meta["top_k"]
+    ws_bytes = api.ws_size(pa, pb, pairs_np, prm)
+    mws = api.Workspace(dev)
+
+    def step():
+        api.similarity(pa, pb, pairs_np, omega, ALPHA, K_ITERS, want_match=False, ws=ws, d_pairs=d_pairs,
+                       out=out, check_status=False, ws_bytes=ws_bytes)
+        top, idx = api.topk(out["scores"].view(nq, nc), k)
+        win = np.stack([np.repeat(np.arange(nq), k), idx.cpu().numpy().ravel()], axis=1).astype(np.int32)
+        api.similarity(pa, pb, win, omega, ALPHA, K_ITERS, want_match=True, ws=mws, check_status=False)
+    return step, P, 4 + 1 + 4
+
+
+def run_workload(args):
+    """--workload cfg3 / cfg4 / cfg5: one JSON line for that workload alone."""
+    import torch
+
+    world, rank, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    step, P, launches = make_step(args.workload, dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    with ClockSampler(local) as clk:
+        ms = timed_steps(step, args.steps, args.warmup, flush, stream)
+    tot = float(sum(ms))
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([tot], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = float(t.item())
+    if rank != 0:
+        return
+    mps = tot / args.steps
+    print(json.dumps({
+        "metric": METRIC, "value": world * P / (mps * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "pairs": P,
+                   "l2": "flushed between steps (256 MiB write, outside the step events)"},
+        "gpu_launches": launches * args.steps, "clocks": clk.summary(),
+    }), flush=True)
+
+
 def run_ours(args):
     import ctypes as C
 
@@ -298,6 +408,11 @@ def run_ours(args):
     torch.cuda.synchronize()
     pp_ms = e0.elapsed_time(e1) / pp_steps
 
+    # ---- forward + adjoint on the gradient workload (256 pairs, n 10-300)
+    fb_step, fb_p, _ = make_step("cfg4", dev)
+    fb_ms = timed_steps(fb_step, 5, 3, flush, stream)
+    fb_mps = float(np.mean(fb_ms))
+
     # ---- end to end through the C ABI with host buffers: build + upload the
     # pack from the host CFG arrays, upload the pairs from pinned memory,
     # compute, read scores and matchings back into pinned memory
@@ -359,6 +474,8 @@ def run_ours(args):
                              "peak_gbs": peaks.get("hbm_gbs"),
                              "frac": (hbm_bytes / (ms_per_step * 1e-3) / 1e9) / peaks["hbm_gbs"]
                              if peaks.get("hbm_gbs") else None, "peak_source": "MEASURED_PEAKS.json (of measured)"}},
+        "fwd_bwd": {"value": fb_p / (fb_mps * 1e-3), "unit": UNIT, "ms_per_step": fb_mps,
+                    "workload": WORKLOADS["cfg4"]},
         "per_pair": {"value": P / (pp_ms * 1e-3), "unit": UNIT, "ms_per_step": pp_ms, "launches_per_step": P,
                      "speedup_batched_over_per_pair": pp_ms / ms_per_step},
         "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -382,11 +499,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", default="cfg2", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "cfg2":
+        run_workload(args)
     else:
         run_ours(args)
 
