@@ -611,58 +611,140 @@ __device__ __forceinline__ void run_pair_s(const Ctx& cx, const Geo& g, const Gr
   grp.sync();
 }
 
-// A global-class pair on the whole CTA: X, Ehat and the matching state in a
-// scratch slot of the workspace.
-__device__ __noinline__ void run_pair_g(const Ctx& cx, const Geo& g, const Group& grp, float* slot) {
-  const int n_row = g.na, n_col = g.nb;  // global-class shapes are never transposed
-  const int64_t E = (int64_t)n_row * n_col;
-  float* b0 = slot;
-  float* b1 = b0 + E;
-  float* eh = b1 + E;
-  float* rn = eh + E;
-  float* cn = rn + n_row;
-  int32_t* ms = reinterpret_cast<int32_t*>(cn + n_col);
-  const int t = grp.rank, G = grp.size;
-  for (int i = t; i < n_row; i += G) rn[i] = attr_norm(g.r_attr + (size_t)i * cx.Fp, cx.om, cx.Fp);
-  for (int jj = t; jj < n_col; jj += G) cn[jj] = attr_norm(g.c_attr + (size_t)jj * cx.Fp, cx.om, cx.Fp);
-  grp.sync();
-  float ss = 0.f;
-  for (int64_t idx = t; idx < E; idx += G) {
-    const int i = (int)(idx / n_col), jj = (int)(idx - (int64_t)i * n_col);
-    const float dot = attr_dot(g.r_attr + (size_t)i * cx.Fp, g.c_attr + (size_t)jj * cx.Fp, cx.om, cx.Fp);
-    const float den = rn[i] * cn[jj];
-    const float e = den > 0.f ? dot / den : 0.f;
-    eh[idx] = e;
-    ss = fmaf(e, e, ss);
+// Calls f(i, j, i * ld + j) for the entries t, t + G, t + 2G, ... of an
+// n_row x n_col matrix in row-major order, stepping (i, j) without a division.
+template <class Fn>
+__device__ __forceinline__ void for_entries(int n_row, int n_col, int ld, int t, int G, Fn&& f) {
+  const int di = G / n_col, dj = G % n_col;
+  for (int i = t / n_col, j = t % n_col; i < n_row;) {
+    f(i, j, (size_t)i * ld + j);
+    i += di;
+    j += dj;
+    if (j >= n_col) {
+      j -= n_col;
+      ++i;
+    }
   }
+}
+
+// A global-class pair on the whole CTA (too large for shared memory): the
+// iterates, (1-alpha) Ehat and the matching state live in a scratch slot of
+// the workspace (L2-resident); the row and column graphs are staged in the
+// CTA's shared memory exactly as for a resident pair, and the gather is the
+// same straight-line code on global addresses.  Columns are spread over
+// C = min(n_col, NT) lanes and rows over NT / C row groups; a thread loops
+// over its columns and rows.  Slot: [ehb | buf0 | buf1] (n_row x n_col
+// floats each), row norms, int32 matching state.
+template <bool kStaged>
+__device__ __noinline__ void run_pair_g(const Ctx& cx, const Geo& g, const Group& grp, float* slot,
+                                        unsigned char* region) {
+  const int n_row = g.na, n_col = g.nb, ld = g.nb;  // global-class shapes are never transposed
+  const size_t E = (size_t)n_row * n_col;
+  float* ehb = slot;
+  float* buf0 = ehb + E;
+  float* buf1 = buf0 + E;
+  float* rn = buf1 + E;
+  int32_t* ms = reinterpret_cast<int32_t*>(rn + n_row + n_col);
+  const int t = grp.rank, G = grp.size;
+  int4* ra = reinterpret_cast<int4*>(region);
+  int4* rq = ra + n_row;
+  int4* rr = rq + n_row;
+  int2* redge = reinterpret_cast<int2*>(rr + n_row);
+
+  // stage both graphs (byte offsets of rows use the global row stride ld);
+  // without staging (graphs too large for shared memory) only the row norms
+  const int eo0 = __ldg(g.r_optr), ei0 = __ldg(g.r_iptr);
+  const int e_row = __ldg(g.r_optr + n_row) - eo0;
+  const int co0 = __ldg(g.c_optr), ci0 = __ldg(g.c_iptr);
+  const int e_col = __ldg(g.c_optr + n_col) - co0;
+  int2* cedge = redge + 2 * e_row;
+  int* cptr = reinterpret_cast<int*>(cedge + 2 * e_col);
+  if (!kStaged)
+    for (int i = t; i < n_row; i += G) rn[i] = attr_norm(g.r_attr + (size_t)i * cx.Fp, cx.om, cx.Fp);
+  for (int i = t; kStaged && i < n_row; i += G) {
+    const int o0 = __ldg(g.r_optr + i) - eo0, o1 = __ldg(g.r_optr + i + 1) - eo0;
+    const int q0 = __ldg(g.r_iptr + i) - ei0, q1 = __ldg(g.r_iptr + i + 1) - ei0;
+    const CfAdj z{0, 0.f};
+    const CfAdj a0 = o1 > o0 ? ldg_adj(g.r_oadj + eo0 + o0) : z, a1 = o1 > o0 + 1 ? ldg_adj(g.r_oadj + eo0 + o0 + 1) : z;
+    const CfAdj b0 = q1 > q0 ? ldg_adj(g.r_iadj + ei0 + q0) : z, b1 = q1 > q0 + 1 ? ldg_adj(g.r_iadj + ei0 + q0 + 1) : z;
+    const int flag = (o1 - o0 > 2 || q1 - q0 > 2) ? (int)0x80000000 : 0;
+    ra[i] = make_int4(4 * ld * a0.nbr, __float_as_int(a0.w), 4 * ld * a1.nbr, __float_as_int(a1.w) | flag);
+    rq[i] = make_int4(4 * ld * b0.nbr, __float_as_int(b0.w), 4 * ld * b1.nbr, __float_as_int(b1.w));
+    rr[i] = make_int4(o0, o1, e_row + q0, e_row + q1);
+    rn[i] = attr_norm(g.r_attr + (size_t)i * cx.Fp, cx.om, cx.Fp);
+  }
+  for (int k = t; kStaged && k < e_row; k += G) {
+    const CfAdj a = ldg_adj(g.r_oadj + eo0 + k), b = ldg_adj(g.r_iadj + ei0 + k);
+    redge[k] = make_int2(4 * ld * a.nbr, __float_as_int(a.w));
+    redge[e_row + k] = make_int2(4 * ld * b.nbr, __float_as_int(b.w));
+  }
+  for (int k = t; kStaged && k < e_col; k += G) {
+    const CfAdj a = ldg_adj(g.c_oadj + co0 + k), b = ldg_adj(g.c_iadj + ci0 + k);
+    cedge[k] = make_int2(4 * a.nbr, __float_as_int(a.w));
+    cedge[e_col + k] = make_int2(4 * b.nbr, __float_as_int(b.w));
+  }
+  for (int k = t; kStaged && k <= n_col; k += G) {
+    cptr[k] = __ldg(g.c_optr + k) - co0;
+    cptr[n_col + 1 + k] = e_col + __ldg(g.c_iptr + k) - ci0;
+  }
+  grp.sync();
+
+  // Entries are visited in row-major order, thread t taking t, t + G, ...:
+  // the whole CTA sweeps a narrow band of rows at a time, so the rows its
+  // gathers read (neighbours of the band) stay cache-resident.  (i, j) of the
+  // next entry follow without a division.
+
+  // a3: E, |E|, Ehat = X_0
+  float ss = 0.f;
+  for_entries(n_row, n_col, ld, t, G, [&](int i, int j, size_t off) {
+    const float* bcol = g.c_attr + (size_t)j * cx.Fp;
+    const float cj = attr_norm(bcol, cx.om, cx.Fp);
+    const float den = rn[i] * cj;
+    const float e = den > 0.f ? attr_dot(g.r_attr + (size_t)i * cx.Fp, bcol, cx.om, cx.Fp) / den : 0.f;
+    ehb[off] = e;
+    ss = fmaf(e, e, ss);
+  });
   const float tot = grp.sum(ss, 0);
   const float inv = tot > 0.f ? 1.0f / sqrtf(tot) : 0.f;
   const float uni = 1.0f / sqrtf((float)n_row * (float)n_col);
-  for (int64_t idx = t; idx < E; idx += G) {
-    const float v = tot > 0.f ? eh[idx] * inv : uni;
-    eh[idx] = v;
-    b0[idx] = v;
-  }
+  const float cb = 1.f - cx.alpha;
+  for_entries(n_row, n_col, ld, t, G, [&](int, int, size_t off) {
+    const float eh = tot > 0.f ? ehb[off] * inv : uni;
+    buf0[off] = eh;
+    ehb[off] = cb * eh;
+  });
   grp.sync();
+
+  // a4: K renormalised iterations, one barrier each
   float sk = 1.f;
-  const float cbl = 1.f - cx.alpha;
   for (int k = 0; k < cx.K; ++k) {
-    const float* cur = (k & 1) ? b1 : b0;
-    float* nxt = (k & 1) ? b0 : b1;
+    const char* cur = reinterpret_cast<const char*>((k & 1) ? buf1 : buf0);
+    float* nxt = (k & 1) ? buf0 : buf1;
     const float ca = 0.5f * cx.alpha * sk;
     ss = 0.f;
-    for (int64_t idx = t; idx < E; idx += G) {
-      const int i = (int)(idx / n_col), jj = (int)(idx - (int64_t)i * n_col);
-      const float y = fmaf(ca, gather_g(cur, n_col, g, i, jj), cbl * eh[idx]);
-      nxt[idx] = y;
+    for_entries(n_row, n_col, ld, t, G, [&](int i, int j, size_t off) {
+      float z;
+      if (kStaged) {
+        const ColPad cl = load_col(cptr, cedge, n_col, j);
+        const int4 A = ra[i], Q = rq[i];
+        z = gather_fast(cur, A, Q, cl);
+        if (A.w < 0 || cl.flag) {
+          const int4 R4 = rr[i];
+          if (A.w < 0) z += row_extra(cur, R4, redge, cl);
+          if (cl.flag) z += col_extra(cur, A, Q, R4, redge, cedge, cl);
+        }
+      } else {
+        z = gather_g(reinterpret_cast<const float*>(cur), ld, g, i, j);
+      }
+      const float y = fmaf(ca, z, ehb[off]);
+      nxt[off] = y;
       ss = fmaf(y, y, ss);
-    }
+    });
     const float yy = grp.sum(ss, (k + 1) & 1);
     sk = cx.norm_mode == 0 ? 1.0f / sqrtf(yy) : 1.f;
   }
-  float* Xs = (cx.K & 1) ? b1 : b0;
-  if (sk != 1.f)
-    for (int64_t idx = t; idx < E; idx += G) Xs[idx] *= sk;
+  float* Xs = (cx.K & 1) ? buf1 : buf0;
+  if (sk != 1.f) for_entries(n_row, n_col, ld, t, G, [&](int, int, size_t off) { Xs[off] *= sk; });
   grp.sync();
   if (cx.X) store_x(grp, cx, g, Xs, n_col);
   if (cx.scores || cx.match) {
@@ -671,6 +753,13 @@ __device__ __noinline__ void run_pair_g(const Ctx& cx, const Geo& g, const Group
     if (cx.scores && t == 0) cx.scores[g.p] = sc;
   }
   grp.sync();
+}
+
+// Whether a global-class pair's graphs can be staged in the CTA's shared memory.
+__device__ __forceinline__ bool staged_fits(const Geo& g, int region) {
+  const int e_row = __ldg(g.r_optr + g.na) - __ldg(g.r_optr);
+  const int e_col = __ldg(g.c_optr + g.nb) - __ldg(g.c_optr);
+  return 48 * (size_t)g.na + 16 * (size_t)(e_row + e_col) + 8 * (size_t)(g.nb + 2) <= (size_t)region;
 }
 
 // Per-CTA setup, done by thread 0 into shared memory (so the pack views do
@@ -751,7 +840,13 @@ __global__ void __launch_bounds__(NT, 1) fwd_batched_kernel(CallArgs a, int per_
         const uint32_t q = s_p[0];
         __syncthreads();
         if (q >= n[kClassGlobal]) break;
-        run_pair_g(cx, make_geo(cx, (int)cx.queue[q], cc, kClassWarp), cta, slot);
+        {
+          const Geo g = make_geo(cx, (int)cx.queue[q], cc, kClassWarp);
+          if (staged_fits(g, cc.z_cta))
+            run_pair_g<true>(cx, g, cta, slot, smem);
+          else
+            run_pair_g<false>(cx, g, cta, slot, smem);
+        }
       }
     }
   }
@@ -787,7 +882,10 @@ __global__ void __launch_bounds__(NT, 1) fwd_batched_kernel(CallArgs a, int per_
         if (global_slot_bytes(g.na, g.nb) > cx.scratch_bytes) {
           if (t == 0) set_status(cx.hdr, 2 /* CF_ERR_WORKSPACE */, per_pair);
         } else {
-          run_pair_g(cx, g, cta, reinterpret_cast<float*>(cx.scratch));
+          if (staged_fits(g, cc.z_cta))
+            run_pair_g<true>(cx, g, cta, reinterpret_cast<float*>(cx.scratch), smem);
+          else
+            run_pair_g<false>(cx, g, cta, reinterpret_cast<float*>(cx.scratch), smem);
         }
         break;
       }

@@ -275,3 +275,14 @@ def test_topk_exact():
         order = np.lexsort((np.arange(Cn), -s[q]))[:k]
         assert np.array_equal(idx[q], order)
         assert np.array_equal(top[q], s[q][order])
+
+
+def test_cfg_too_large_to_stage():
+    # a 4,500-block CFG: its pairs are global-class and its graph does not fit
+    # the staging area, so the gather reads the pack directly
+    rng = np.random.default_rng(99)
+    big = structured_cfg(rng, 4500, 6, 12)
+    small = [structured_cfg(rng, n, 3, 12) for n in (5, 9)]
+    cfgs = [big] + small
+    pairs = np.array([(0, 1), (2, 0), (0, 2)], np.int32)
+    compare(cfgs, cfgs, pairs, 13)
