@@ -16,3 +16,4 @@ from .isorank import (  # noqa: F401
     score_gradient,
     similarity,
 )
+from . import distances  # noqa: F401,E402  (interpolation + Table 1 distances)
