@@ -17,3 +17,4 @@ from .isorank import (  # noqa: F401
     similarity,
 )
 from . import distances  # noqa: F401,E402  (interpolation + Table 1 distances)
+from . import ward  # noqa: F401,E402  (Ward clustering of similarity profiles)
