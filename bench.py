@@ -26,6 +26,7 @@ import re  # noqa: E402
 import statistics  # noqa: E402
 import subprocess  # noqa: E402
 import sys  # noqa: E402
+import tempfile  # noqa: E402
 import threading  # noqa: E402
 import time  # noqa: E402
 
@@ -242,9 +243,9 @@ def timed_steps(step, steps, warmup, flush, stream):
     return [e0.elapsed_time(e1) for e0, e1 in ev]
 
 
-def make_step(name, dev):
-    """The step of one workload through the Python API: returns (step, n_pairs,
-    launches_per_step)."""
+def make_step(name, dev, tune_cache=None):
+    """The step of one workload through the Python API (kernel configuration
+    from the autotuner): returns (step, n_pairs, launches_per_step, tune)."""
     import torch
 
     from paper_1707_02423_gb300 import _binding as B
@@ -262,13 +263,14 @@ def make_step(name, dev):
     x_off, m_off = api.out_offsets(pa, pb, pairs_np)
     out = {"scores": torch.empty(P, dtype=torch.float32, device=dev),
            "match": torch.empty(int(m_off[-1]), dtype=torch.int32, device=dev)}
+    tune, _ = api.autotune(pa, pb, pairs_np, omega, ALPHA, K_ITERS, cache_path=tune_cache)
     if name in ("cfg2", "cfg3"):
         ws_bytes = api.ws_size(pa, pb, pairs_np, prm)
 
         def step():
             api.similarity(pa, pb, pairs_np, omega, ALPHA, K_ITERS, want_match=True, ws=ws, d_pairs=d_pairs,
-                           out=out, check_status=False, ws_bytes=ws_bytes)
-        return step, P, 4
+                           out=out, check_status=False, ws_bytes=ws_bytes, tune=tune)
+        return step, P, 4, tune
     if name == "cfg4":
         ws_bytes = api.ws_size(pa, pb, pairs_np, prm)
         bws = api.Workspace(dev)
@@ -276,9 +278,9 @@ def make_step(name, dev):
 
         def step():
             api.similarity(pa, pb, pairs_np, omega, ALPHA, K_ITERS, want_match=True, ws=ws, d_pairs=d_pairs,
-                           out=out, check_status=False, ws_bytes=ws_bytes)
+                           out=out, check_status=False, ws_bytes=ws_bytes, tune=tune)
             api.similarity_backward(pa, pb, pairs_np, omega, out["match"], g, ALPHA, K_ITERS, ws=bws)
-        return step, P, 4 + 7
+        return step, P, 4 + 7, tune
     # cfg5: scores of every query-corpus pair, top-16 per query, matchings of the winners
     nq, nc, k = w.meta["n_query"], w.meta["n_corpus"], w.meta["top_k"]
     ws_bytes = api.ws_size(pa, pb, pairs_np, prm)
@@ -286,20 +288,22 @@ def make_step(name, dev):
 
     def step():
         api.similarity(pa, pb, pairs_np, omega, ALPHA, K_ITERS, want_match=False, ws=ws, d_pairs=d_pairs,
-                       out=out, check_status=False, ws_bytes=ws_bytes)
+                       out=out, check_status=False, ws_bytes=ws_bytes, tune=tune)
         top, idx = api.topk(out["scores"].view(nq, nc), k)
         win = np.stack([np.repeat(np.arange(nq), k), idx.cpu().numpy().ravel()], axis=1).astype(np.int32)
-        api.similarity(pa, pb, win, omega, ALPHA, K_ITERS, want_match=True, ws=mws, check_status=False)
-    return step, P, 4 + 1 + 4
+        api.similarity(pa, pb, win, omega, ALPHA, K_ITERS, want_match=True, ws=mws, check_status=False, tune=tune)
+    return step, P, 4 + 1 + 4, tune
 
 
 def run_workload(args):
     """--workload cfg3 / cfg4 / cfg5: one JSON line for that workload alone."""
     import torch
 
+    from paper_1707_02423_gb300 import api
+
     world, rank, local = dist_setup(args.gpus)
     dev = torch.device("cuda", torch.cuda.current_device())
-    step, P, launches = make_step(args.workload, dev)
+    step, P, launches, tune = make_step(args.workload, dev, args.tune_cache)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     with ClockSampler(local) as clk:
@@ -319,7 +323,8 @@ def run_workload(args):
         "warmup": args.warmup, "ms_per_step": mps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "pairs": P,
-                   "l2": "flushed between steps (256 MiB write, outside the step events)"},
+                   "l2": "flushed between steps (256 MiB write, outside the step events)",
+                   "tune": api.tune_info(tune)},
         "gpu_launches": launches * args.steps, "clocks": clk.summary(),
     }), flush=True)
 
@@ -349,17 +354,30 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
+    # on-chip peak the iteration kernel is bound by, measured on this GPU
+    smem_probe = api.probe(B.CF_PROBE_SMEM, reps=3)
+    # kernel configuration: the autotuner's pick for this workload (cached per device and workload)
+    tune, tune_ms = api.autotune(pack, pack, pairs_np, omega, ALPHA, K_ITERS, cache_path=args.tune_cache)
+
     def sim(flags):
         api.similarity(pack, pack, pairs_np, omega, ALPHA, K_ITERS, want_match=True, ws=ws, d_pairs=d_pairs,
-                       out=out, check_status=False, flags=flags, ws_bytes=ws_bytes)
+                       out=out, check_status=False, flags=flags, ws_bytes=ws_bytes, tune=tune)
 
-    def step():
+    # one step = the plan graph (workspace reset + 3 plan kernels) and the
+    # forward graph (queue reset + the persistent kernel), each captured once
+    sim(B.CF_FLAG_PLAN_ONLY)
+    sim(B.CF_FLAG_REUSE_PLAN)
+    torch.cuda.synchronize()
+    g_plan, g_fwd = api.Graph(dev), api.Graph(dev)
+    with g_plan.capture():
         sim(B.CF_FLAG_PLAN_ONLY)
+    with g_fwd.capture():
         sim(B.CF_FLAG_REUSE_PLAN)
 
     for _ in range(args.warmup):
         flush.zero_()
-        step()
+        g_plan.launch(stream)
+        g_fwd.launch(stream)
     B.check(B.lib().cf_status_check(ws.get(ws_bytes).data_ptr(), int(stream.cuda_stream)))
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     if world > 1:
@@ -372,9 +390,9 @@ def run_ours(args):
         for i in range(args.steps):
             flush.zero_()  # outside the step's events
             ev[i][0].record(stream)
-            sim(B.CF_FLAG_PLAN_ONLY)
+            g_plan.launch(stream)
             ev[i][1].record(stream)
-            sim(B.CF_FLAG_REUSE_PLAN)
+            g_fwd.launch(stream)
             ev[i][2].record(stream)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
@@ -396,20 +414,20 @@ def run_ours(args):
     pp_steps = 2
     for _ in range(1):
         api.similarity(pack, pack, pairs_np, omega, ALPHA, K_ITERS, want_match=True, ws=ws, d_pairs=d_pairs,
-                       out=out, check_status=False, per_pair=True, ws_bytes=ws_bytes)
+                       out=out, check_status=False, per_pair=True, ws_bytes=ws_bytes, tune=tune)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(pp_steps):
         flush.zero_()
         api.similarity(pack, pack, pairs_np, omega, ALPHA, K_ITERS, want_match=True, ws=ws, d_pairs=d_pairs,
-                       out=out, check_status=False, per_pair=True, ws_bytes=ws_bytes)
+                       out=out, check_status=False, per_pair=True, ws_bytes=ws_bytes, tune=tune)
     e1.record(stream)
     torch.cuda.synchronize()
     pp_ms = e0.elapsed_time(e1) / pp_steps
 
     # ---- forward + adjoint on the gradient workload (256 pairs, n 10-300)
-    fb_step, fb_p, _ = make_step("cfg4", dev)
+    fb_step, fb_p, _, _ = make_step("cfg4", dev, args.tune_cache)
     fb_ms = timed_steps(fb_step, 5, 3, flush, stream)
     fb_mps = float(np.mean(fb_ms))
 
@@ -417,6 +435,7 @@ def run_ours(args):
     # pack from the host CFG arrays, upload the pairs from pinned memory,
     # compute, read scores and matchings back into pinned memory
     L = B.lib()
+    prm.tune = tune
     pairs_pin = torch.from_numpy(pairs_np).pin_memory()
     sc_pin = torch.empty(P, dtype=torch.float32).pin_memory()
     mt_pin = torch.empty(int(m_off[-1]), dtype=torch.int32).pin_memory()
@@ -449,8 +468,9 @@ def run_ours(args):
     clk = clk.summary()
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
-    f_mhz = clk["sm_mhz"] or measured_peaks().get("clocks_under_load", {}).get("sm_mhz_median", 1432.0)
-    smem_peak_gbs = 128.0 * n_sm * f_mhz * 1e6 / 1e9  # 128 B/clk/SM shared-memory bandwidth
+    f_mhz = clk["sm_mhz"] or smem_probe["sm_mhz"]
+    # measured shared-memory bytes per clock per SM, at the SM clock sampled during the timed region
+    smem_peak_gbs = smem_probe["per_clk_sm"] * n_sm * f_mhz * 1e6 / 1e9
     achieved = onchip / fwd_mean_s / 1e9
     peaks = measured_peaks()
     hbm_bytes = int(pack.host.size + pairs_np.nbytes + P * 4 + m_elems * 4)
@@ -462,11 +482,15 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "pairs": P, "n_cfgs": len(w.cfgs_a), "F": w.F, "K": K_ITERS,
                    "alpha": ALPHA, "l2": "flushed between steps (256 MiB write, outside the step events)",
-                   "step": "plan kernels + persistent forward kernel (sum of per-step CUDA events)"},
+                   "step": "two CUDA-graph launches: plan (workspace reset + 3 kernels), forward (queue reset + "
+                           "persistent kernel); sum of per-step CUDA events",
+                   "tune": {**api.tune_info(tune), "autotune_sample_ms": tune_ms}},
         "roofline": {"bound": "smem", "kernel": "fwd_batched_kernel", "achieved": achieved,
                      "peak": smem_peak_gbs, "unit": "GB/s", "frac": achieved / smem_peak_gbs,
                      "traffic": traffic,
-                     "peak_source": f"derived: 128 B/clk/SM x {n_sm} SMs x {f_mhz:.0f} MHz (median SM clock sampled)",
+                     "peak_source": f"of measured: cf_probe shared-memory loads {smem_probe['per_clk_sm']:.1f} "
+                                    f"B/clk/SM ({smem_probe['rate'] / 1e9:.0f} GB/s at {smem_probe['sm_mhz']:.0f} MHz) "
+                                    f"x {n_sm} SMs x {f_mhz:.0f} MHz (median SM clock sampled in the timed region)",
                      "algorithmic_bytes_per_launch": onchip, "kernel_ms": fwd_mean_s * 1e3,
                      "flops_per_launch": flops, "achieved_tflops_fp32": flops / fwd_mean_s / 1e12,
                      "hbm": {"algorithmic_bytes_per_step": hbm_bytes,
@@ -500,6 +524,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="cfg2", choices=sorted(WORKLOADS))
+    ap.add_argument("--tune-cache", default=os.environ.get("CF_AUTOTUNE_CACHE") or
+                    os.path.join(tempfile.gettempdir(), "cfsim_autotune.cache"))
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -72,7 +72,10 @@ typedef enum cf_status {
 enum { CF_NORM_FROB = 0, /* X_{k+1} = Y_{k+1} / |Y_{k+1}|_F (the method)                */
        CF_NORM_NONE = 1  /* X_{k+1} = Y_{k+1}: plain fixed-point iteration of the Table 1
                             linear system (I - alpha M) x = (1 - alpha) vec Ehat; for tests */ };
-enum { CF_MATCH_GREEDY = 0 };
+enum { CF_MATCH_GREEDY = 0,  /* greedy: largest remaining entry first (the default)      */
+       CF_MATCH_OPTIMAL = 1  /* maximum-weight assignment of min(n_a, n_b) pairs (the
+                                "best matching" alternative; Hungarian method, one warp
+                                per pair); needs the matrices (d_X), CFGs <= 9000 blocks */ };
 
 /* flags */
 enum {
@@ -88,8 +91,10 @@ typedef struct cf_params {
   float alpha;        /* restart blend, 0 <= alpha < 1 (default 0.8)            */
   int32_t K;          /* iterations, K >= 0 (default 40)                         */
   int32_t norm_mode;  /* CF_NORM_FROB (default) or CF_NORM_NONE                   */
-  int32_t match_mode; /* CF_MATCH_GREEDY                                          */
+  int32_t match_mode; /* CF_MATCH_GREEDY (default) or CF_MATCH_OPTIMAL               */
   uint32_t flags;     /* CF_FLAG_*                                                */
+  int32_t tune;       /* kernel configuration: 0 = built-in default, else an id in
+                         [1, cf_num_tunes()] (cf_autotune picks one)              */
 } cf_params;
 
 /* One CFG on the host: blocks 0..n_blocks-1, edges src[e] -> dst[e] with weight
@@ -169,15 +174,20 @@ cf_status cf_similarity_ws_size(const void* h_pack_a, const void* h_pack_b, cons
  * d_X (layout above), d_scores [P], d_match (layout above).  All pairs run in
  * one batched, load-balanced pass (persistent kernels pulling pairs from a
  * cost-ordered queue) unless params->flags has CF_FLAG_PER_PAIR_LAUNCH.
+ * With params->match_mode == CF_MATCH_OPTIMAL the matching and score are the
+ * maximum-weight assignment on the written d_X, which is then required.
  * P == 0 is a no-op. */
 cf_status cf_similarity(const void* d_pack_a, const void* d_pack_b, const int32_t* d_pairs, int32_t P,
                         const cf_params* params, const float* d_omega, float* d_X, float* d_scores,
                         int32_t* d_match, void* d_ws, size_t ws_bytes, cf_stream_t stream);
 
-/* Greedy matching and graph score.  With d_X_in == NULL the similarity is
+/* Node matching and graph score.  With d_X_in == NULL the similarity is
  * recomputed (same as cf_similarity with d_match / d_scores).  With d_X_in
  * given (layout of cf_similarity's d_X) only the matching runs on those
- * matrices; params and d_omega are then unused and may be NULL. */
+ * matrices: greedy, or the maximum-weight assignment when params is given
+ * with match_mode CF_MATCH_OPTIMAL (params is otherwise unused and may be
+ * NULL, as may d_omega).  A pair with a CFG above 9000 blocks under
+ * CF_MATCH_OPTIMAL is skipped and the status word gets CF_ERR_UNSUPPORTED. */
 cf_status cf_match(const void* d_pack_a, const void* d_pack_b, const int32_t* d_pairs, int32_t P,
                    const cf_params* params, const float* d_omega, const float* d_X_in, int32_t* d_match,
                    float* d_scores, void* d_ws, size_t ws_bytes, cf_stream_t stream);
@@ -206,6 +216,59 @@ cf_status cf_similarity_backward(const void* d_pack_a, const void* d_pack_b, con
 cf_status cf_topk(const float* d_scores, int32_t Q, int32_t C, int32_t k, float* d_top, int32_t* d_idx,
                   cf_stream_t stream);
 
+/* ---- the element-wise distances of Table 1 --------------------------------- */
+/* The paper's other family of measures (Sec. 4, 4.1, Table 1): the smaller
+ * CFG's transition matrix (T[s, d] = weight of edge s -> d, duplicates added)
+ * is resized by bilinear interpolation to N = max(n_a, n_b) -- output index t
+ * samples the source at t (n - 1) / (N - 1), so corners are kept; a 1 x 1
+ * matrix stays constant; equal sizes are not resized -- and five distances
+ * are taken between the two N x N matrices x (resized) and y:
+ *   CF_DIST_EUCLIDEAN  sqrt(sum (x - y)^2)
+ *   CF_DIST_MANHATTAN  sum |x - y|
+ *   CF_DIST_MINKOWSKI  (sum |x - y|^p)^(1/p)
+ *   CF_DIST_JACCARD    sum (x - y)^2 / (sum x^2 + sum y^2 - sum x y)   (0 if the
+ *                      denominator is 0)
+ *   CF_DIST_COSINE     1 - sum x y / (|x| |y|)   (0 if both norms are 0, 1 if one is)
+ * With CF_DIST_SCALE01 every distance is min-max scaled to [0, 1] over the
+ * call's P pairs (Sec. 5.2: 0 = strongest similarity; a constant distance
+ * scales to 0).  d_out: float [P][5] in the order above.  0 < p <= 64.  CFGs
+ * up to 28,000 blocks (larger: status word CF_ERR_UNSUPPORTED); a pair index
+ * out of range: status word CF_ERR_INVALID_ARG (read with cf_status_check on
+ * d_ws).  d_ws: cf_distances_ws_size bytes. */
+enum { CF_DIST_EUCLIDEAN = 0, CF_DIST_MANHATTAN = 1, CF_DIST_MINKOWSKI = 2, CF_DIST_JACCARD = 3, CF_DIST_COSINE = 4,
+       CF_DIST_COUNT = 5 };
+enum { CF_DIST_SCALE01 = 1u };
+cf_status cf_distances_ws_size(int32_t P, size_t* bytes);
+cf_status cf_distances(const void* d_pack_a, const void* d_pack_b, const int32_t* d_pairs, int32_t P, float p,
+                       uint32_t flags, float* d_out, void* d_ws, size_t ws_bytes, cf_stream_t stream);
+
+/* ---- Ward clustering of similarity profiles -------------------------------- */
+/* Sec. 5.3 groups kernels with Ward's minimum-variance method on squared
+ * Euclidean distances between points.  A CFG's point is its row of the
+ * all-pairs score matrix (its similarity profile); cf_score_matrix builds that
+ * matrix from a pair list and its scores.
+ *
+ * cf_score_matrix: zero d_S [n_rows x n_cols] (row-major), then
+ * S[a][b] = d_scores[p] for every pair p = (a, b) of d_pairs, and S[b][a] too
+ * when symmetric (n_rows == n_cols).  *d_status (one int32 on the device)
+ * becomes 0, or 1 + the index of a pair out of range (that pair is skipped).
+ *
+ * cf_ward: agglomerative Ward clustering of n points d_points [n x dim]
+ * (row-major), n <= 16384: n - 1 merges in scipy's linkage convention --
+ * merge k joins clusters d_merge[2k] < d_merge[2k+1] (ids below n are points,
+ * n + k the cluster formed at merge k) at height d_height[k] (the Ward
+ * distance, sqrt of the Lance-Williams-updated squared distance) into
+ * d_size[k] points.  Ties: the pair of smallest (slot, slot) index.  Runs the
+ * distance matrix on the whole GPU, then the merges on one CTA (L2-resident
+ * matrix, per-row minimum cache).  d_ws: cf_ward_ws_size bytes (4 n^2 + O(n));
+ * its first word is a status word (cf_status_check): CF_ERR_NUMERIC if the
+ * points hold NaN. */
+cf_status cf_score_matrix(const int32_t* d_pairs, const float* d_scores, int32_t P, int32_t n_rows, int32_t n_cols,
+                          int32_t symmetric, float* d_S, int32_t* d_status, cf_stream_t stream);
+cf_status cf_ward_ws_size(int32_t n, size_t* bytes);
+cf_status cf_ward(const float* d_points, int32_t n, int32_t dim, int32_t* d_merge, float* d_height, int32_t* d_size,
+                  void* d_ws, size_t ws_bytes, cf_stream_t stream);
+
 /* ---- no-allocation variant ------------------------------------------------- */
 /* cf_similarity without a workspace argument, for callers that cannot
  * allocate device memory (code running under an allocator that owns the whole
@@ -229,6 +292,108 @@ cf_status cf_topk(const float* d_scores, int32_t Q, int32_t C, int32_t k, float*
 cf_status cf_similarity_noalloc(const void* d_pack_a, const void* d_pack_b, const int32_t* d_pairs, int32_t P,
                                 const cf_params* params, const float* d_omega, float* d_X, float* d_scores,
                                 int32_t* d_match, int32_t* d_status, cf_stream_t stream);
+
+/* ---- a7: autotuner --------------------------------------------------------- */
+/* Kernel configurations of the batched forward, by tune id (cf_params.tune):
+ * threads per CTA (1024 or 512), the smallest thread group a pair may be
+ * given (a warp, a quarter CTA, or the whole CTA), the matching policy of
+ * shared-memory-resident pairs (ranked lists wherever their state fits, only
+ * below the whole-CTA level, or never: rounds of rescans), and the cluster
+ * tier: pairs too large for one CTA split by rows over the 2, 4 or 8 CTAs of
+ * a thread-block cluster with the iterates in distributed shared memory (or,
+ * with no cluster tier, iterated by one CTA out of L2).  Every tune gives the
+ * same results up to rounding; only the speed differs. */
+typedef struct cf_tune_info {
+  int32_t tune;
+  int32_t threads_per_cta; /* 1024 or 512                                     */
+  int32_t smallest_group;  /* threads: 32, threads_per_cta / 4 or threads_per_cta */
+  int32_t matching;        /* 0 ranked where it fits, 1 ranked below the whole
+                              CTA, 2 rescans only                               */
+  int32_t cluster;         /* CTAs per thread-block cluster of the cluster tier
+                              (0: none; pairs too large for one CTA then use the
+                              global-memory tier)                               */
+} cf_tune_info;
+int32_t cf_num_tunes(void);
+cf_status cf_tune_describe(int32_t tune, cf_tune_info* out);
+
+/* Workspace bytes cf_autotune needs for this pair list (host copies). */
+cf_status cf_autotune_ws_size(const void* h_pack_a, const void* h_pack_b, const int32_t* h_pairs, int32_t P,
+                              const cf_params* params, size_t* bytes);
+
+/* Pick the fastest tune for this workload: time cf_similarity (scores and
+ * matchings) under every tune on a deterministic sample of at most 16384 of
+ * the pairs (pair floor(k P / S), k < S), one warm-up and three timed calls
+ * each, and return the fastest in *tune (its time in *best_ms, may be NULL).
+ * The choice is cached in the text file cache_path (or, when NULL, in the file
+ * named by the environment variable CF_AUTOTUNE_CACHE; no caching if neither
+ * is set) under a key of device name, SM count, F_pad, K, norm_mode and the
+ * sample's cost distribution; a cache hit returns at once without device work.
+ * Host copies (h_pack_*, h_pairs) size and key the run, device copies run it.
+ * BLOCKS.  d_ws: cf_autotune_ws_size bytes, contents overwritten. */
+cf_status cf_autotune(const void* h_pack_a, const void* h_pack_b, const void* d_pack_a, const void* d_pack_b,
+                      const int32_t* h_pairs, int32_t P, const cf_params* params, const float* d_omega, void* d_ws,
+                      size_t ws_bytes, const char* cache_path, cf_stream_t stream, int32_t* tune, float* best_ms);
+
+/* ---- a7: CUDA-graph capture --------------------------------------------- */
+/* A batch step (plan kernels, persistent forward, top-k, matching of the
+ * winners, ...) recorded once and replayed as one graph launch, so the
+ * per-step cost is one host call whatever the number of kernels.
+ *   cf_graph_begin(stream)      starts capturing `stream` (thread-local mode);
+ *                               `stream` must be a created stream, not NULL
+ *   ... cfsim calls that enqueue on `stream` (cf_similarity, cf_match,
+ *       cf_similarity_backward, cf_topk) ...
+ *   cf_graph_end(stream, &g)    ends the capture and instantiates it; fails
+ *                               with CF_ERR_CUDA if a call that cannot be
+ *                               captured ran in between (anything documented
+ *                               as BLOCKS, e.g. cf_status_check, cf_pack_cfgs)
+ *   cf_graph_launch(g, stream)  replays on any stream (same pointers, same
+ *                               sizes: the buffers named while capturing must
+ *                               stay allocated while g exists)
+ *   cf_graph_destroy(g)
+ * Make one uncaptured call of each kind first: the first use of a kernel
+ * sets its attributes, which must not happen during a capture.  The graph
+ * handle is host memory owned by the library until cf_graph_destroy. */
+typedef struct cf_graph_s* cf_graph;
+cf_status cf_graph_begin(cf_stream_t stream);
+cf_status cf_graph_end(cf_stream_t stream, cf_graph* out);
+cf_status cf_graph_launch(cf_graph g, cf_stream_t stream);
+/* Nodes of the captured graph (kernels and memsets), -1 for NULL. */
+int32_t cf_graph_nodes(cf_graph g);
+cf_status cf_graph_destroy(cf_graph g);
+
+/* ---- measurement: on-chip peaks ------------------------------------------- */
+/* The similarity iterations are bound by on-chip memory, not HBM, so their
+ * roofline needs on-chip peaks.  Each probe is a kernel that does only one
+ * thing, launched on two CTAs per SM:
+ *   CF_PROBE_SMEM   shared-memory loads, 128-bit, conflict-free     (bytes/s)
+ *   CF_PROBE_L2     re-reads of an L2-resident buffer (128 KB per SM) with
+ *                   volatile loads (L1 bypassed)                     (bytes/s)
+ *   CF_PROBE_DSMEM  loads from the partner CTA's shared memory in 2-CTA
+ *                   thread-block clusters                            (bytes/s)
+ *   CF_PROBE_FP32   independent FP32 FMA chains, 2 FLOPs per FMA     (FLOP/s)
+ * The SM clock of the same launch is read on the device (clock64 cycles over
+ * %globaltimer nanoseconds, median over CTAs), so per_clk_sm can be rescaled
+ * to the clock another kernel ran at. */
+enum { CF_PROBE_SMEM = 0, CF_PROBE_L2 = 1, CF_PROBE_DSMEM = 2, CF_PROBE_FP32 = 3 };
+
+typedef struct cf_probe_result {
+  double work;       /* bytes (FLOPs) one probe launch moves (computes)            */
+  double best_ms;    /* fastest timed launch (CUDA events on the caller's stream)  */
+  double rate;       /* work / best_ms, per second                                  */
+  double sm_mhz;     /* SM clock during that launch                                 */
+  double per_clk_sm; /* rate / (sm_mhz * n_sm): bytes (FLOPs) per clock per SM      */
+  int32_t n_sm;      /* SMs of the current device                                   */
+} cf_probe_result;
+
+/* Workspace bytes of a probe on the current device (a few hundred bytes; about
+ * 19 MB for CF_PROBE_L2 on 152 SMs). */
+cf_status cf_probe_ws_size(int32_t kind, size_t* bytes);
+
+/* Run probe `kind` once to warm up and then `reps` times (1..1000) on `stream`,
+ * and report the fastest launch.  BLOCKS (synchronises `stream` after every
+ * launch).  d_ws: at least cf_probe_ws_size bytes, contents overwritten. */
+cf_status cf_probe(int32_t kind, void* d_ws, size_t ws_bytes, int32_t reps, cf_stream_t stream,
+                   cf_probe_result* out);
 
 /* ---- status word ---------------------------------------------------------- */
 /* Read the device status word of the last call that used d_ws.  BLOCKS

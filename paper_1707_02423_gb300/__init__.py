@@ -11,7 +11,7 @@ def __getattr__(name):
     # the torch-facing API is imported lazily so that the build step and the
     # CPU-only ABI checks do not need a CUDA device
     if name in ("Pack", "Workspace", "Result", "similarity", "match", "topk", "out_offsets", "ws_size",
-                "similarity_backward", "CFSimilarity"):
+                "similarity_backward", "CFSimilarity", "Graph", "probe", "autotune", "tune_info", "distances", "score_matrix", "ward"):
         from . import api
 
         return getattr(api, name)

@@ -14,9 +14,13 @@ CF_OK = 0
 CF_NORM_FROB = 0
 CF_NORM_NONE = 1
 CF_MATCH_GREEDY = 0
+CF_MATCH_OPTIMAL = 1
 CF_FLAG_PER_PAIR_LAUNCH = 1
 CF_FLAG_PLAN_ONLY = 2
 CF_FLAG_REUSE_PLAN = 4
+CF_PROBE_SMEM, CF_PROBE_L2, CF_PROBE_DSMEM, CF_PROBE_FP32 = 0, 1, 2, 3
+CF_DIST_SCALE01 = 1
+DIST_NAMES = ("euclidean", "manhattan", "minkowski", "jaccard", "cosine")
 
 
 class cf_cfg_view(C.Structure):
@@ -26,7 +30,17 @@ class cf_cfg_view(C.Structure):
 
 class cf_params(C.Structure):
     _fields_ = [("alpha", C.c_float), ("K", C.c_int32), ("norm_mode", C.c_int32), ("match_mode", C.c_int32),
-                ("flags", C.c_uint32)]
+                ("flags", C.c_uint32), ("tune", C.c_int32)]
+
+
+class cf_probe_result(C.Structure):
+    _fields_ = [("work", C.c_double), ("best_ms", C.c_double), ("rate", C.c_double), ("sm_mhz", C.c_double),
+                ("per_clk_sm", C.c_double), ("n_sm", C.c_int32)]
+
+
+class cf_tune_info(C.Structure):
+    _fields_ = [("tune", C.c_int32), ("threads_per_cta", C.c_int32), ("smallest_group", C.c_int32),
+                ("matching", C.c_int32), ("cluster", C.c_int32)]
 
 
 class cf_pack_info(C.Structure):
@@ -59,6 +73,23 @@ SIGNATURES = {
     "cf_topk": (_i32, [_p, _i32, _i32, _i32, _p, _p, _p]),
     "cf_similarity_noalloc": (_i32, [_p, _p, _p, _i32, C.POINTER(cf_params), _p, _p, _p, _p, _p, _p]),
     "cf_status_check": (_i32, [_p, _p]),
+    "cf_distances_ws_size": (_i32, [_i32, _szp]),
+    "cf_distances": (_i32, [_p, _p, _p, _i32, C.c_float, C.c_uint32, _p, _p, C.c_size_t, _p]),
+    "cf_score_matrix": (_i32, [_p, _p, _i32, _i32, _i32, _i32, _p, _p, _p]),
+    "cf_ward_ws_size": (_i32, [_i32, _szp]),
+    "cf_ward": (_i32, [_p, _i32, _i32, _p, _p, _p, _p, C.c_size_t, _p]),
+    "cf_num_tunes": (_i32, []),
+    "cf_tune_describe": (_i32, [_i32, C.POINTER(cf_tune_info)]),
+    "cf_autotune_ws_size": (_i32, [_p, _p, _p, _i32, C.POINTER(cf_params), _szp]),
+    "cf_autotune": (_i32, [_p, _p, _p, _p, _p, _i32, C.POINTER(cf_params), _p, _p, C.c_size_t, C.c_char_p, _p,
+                           C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
+    "cf_graph_begin": (_i32, [_p]),
+    "cf_graph_end": (_i32, [_p, C.POINTER(C.c_void_p)]),
+    "cf_graph_launch": (_i32, [_p, _p]),
+    "cf_graph_nodes": (_i32, [_p]),
+    "cf_graph_destroy": (_i32, [_p]),
+    "cf_probe_ws_size": (_i32, [_i32, _szp]),
+    "cf_probe": (_i32, [_i32, _p, C.c_size_t, _i32, _p, C.POINTER(cf_probe_result)]),
 }
 
 
@@ -97,5 +128,6 @@ def check(status: int) -> None:
         raise CfsimError(status, f"{msg}: {detail}" if detail else msg)
 
 
-def params(alpha: float = 0.8, K: int = 40, norm_mode: int = CF_NORM_FROB, flags: int = 0) -> cf_params:
-    return cf_params(float(alpha), int(K), int(norm_mode), CF_MATCH_GREEDY, int(flags))
+def params(alpha: float = 0.8, K: int = 40, norm_mode: int = CF_NORM_FROB, flags: int = 0, tune: int = 0,
+           match_mode: int = CF_MATCH_GREEDY) -> cf_params:
+    return cf_params(float(alpha), int(K), int(norm_mode), int(match_mode), int(flags), int(tune))

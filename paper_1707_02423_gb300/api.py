@@ -6,6 +6,7 @@ device.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 from dataclasses import dataclass
 
@@ -127,7 +128,7 @@ def similarity(pa: Pack, pb: Pack, pairs, omega: torch.Tensor, alpha: float = 0.
                want_x: bool = False, want_scores: bool = True, want_match: bool = False, per_pair: bool = False,
                norm_mode: int = B.CF_NORM_FROB, ws: Workspace | None = None, d_pairs: torch.Tensor | None = None,
                out: dict | None = None, stream=None, check_status: bool = True, flags: int = 0,
-               ws_bytes: int | None = None) -> Result:
+               ws_bytes: int | None = None, tune: int = 0, optimal: bool = False) -> Result:
     """X_K, graph scores and greedy matchings for every pair (cf_similarity).
 
     ``pairs``: int [P, 2] host array of (CFG of pa, CFG of pb).  ``omega``: float32
@@ -137,7 +138,9 @@ def similarity(pa: Pack, pb: Pack, pairs, omega: torch.Tensor, alpha: float = 0.
     pairs_np = _pairs_np(pairs)
     P = len(pairs_np)
     dev = pa.dev.device
-    prm = B.params(alpha, K, norm_mode, (B.CF_FLAG_PER_PAIR_LAUNCH if per_pair else 0) | flags)
+    prm = B.params(alpha, K, norm_mode, (B.CF_FLAG_PER_PAIR_LAUNCH if per_pair else 0) | flags, tune,
+                   B.CF_MATCH_OPTIMAL if optimal else B.CF_MATCH_GREEDY)
+    want_x = want_x or (optimal and (want_scores or want_match))  # the assignment runs on X
     x_off, m_off = out_offsets(pa, pb, pairs_np)
     out = {} if out is None else out
     scores = out.get("scores") if want_scores else None
@@ -163,8 +166,36 @@ def similarity(pa: Pack, pb: Pack, pairs, omega: torch.Tensor, alpha: float = 0.
     return Result(scores, match, X, x_off, m_off)
 
 
-def match(pa: Pack, pb: Pack, pairs, X: torch.Tensor, *, ws: Workspace | None = None, stream=None) -> Result:
-    """Greedy matching and scores of caller-given matrices (cf_match with X)."""
+def autotune(pa: Pack, pb: Pack, pairs, omega: torch.Tensor, alpha: float = 0.8, K: int = 40, *,
+             norm_mode: int = B.CF_NORM_FROB, cache_path: str | None = None, stream=None):
+    """The fastest kernel configuration for this workload (cf_autotune):
+    returns ``(tune, ms)``; pass ``tune`` to ``similarity``."""
+    L = B.lib()
+    pairs_np = _pairs_np(pairs)
+    prm = B.params(alpha, K, norm_mode)
+    n = C.c_size_t(0)
+    B.check(L.cf_autotune_ws_size(pa.host_ptr, pb.host_ptr, pairs_np.ctypes.data, len(pairs_np), C.byref(prm),
+                                  C.byref(n)))
+    ws = torch.empty(max(int(n.value), 256), dtype=torch.uint8, device=pa.dev.device)
+    t = C.c_int32(0)
+    ms = C.c_float(0.0)
+    B.check(L.cf_autotune(pa.host_ptr, pb.host_ptr, pa.dev.data_ptr(), pb.dev.data_ptr(), pairs_np.ctypes.data,
+                          len(pairs_np), C.byref(prm), omega.contiguous().data_ptr(), ws.data_ptr(), ws.numel(),
+                          cache_path.encode() if cache_path else None, _stream_ptr(stream), C.byref(t), C.byref(ms)))
+    return int(t.value), float(ms.value)
+
+
+def tune_info(tune: int) -> dict:
+    r = B.cf_tune_info()
+    B.check(B.lib().cf_tune_describe(int(tune), C.byref(r)))
+    return {"tune": r.tune, "threads_per_cta": r.threads_per_cta, "smallest_group": r.smallest_group,
+            "matching": ("ranked", "ranked below the whole CTA", "rescans")[r.matching], "cluster": r.cluster}
+
+
+def match(pa: Pack, pb: Pack, pairs, X: torch.Tensor, *, ws: Workspace | None = None, stream=None,
+          optimal: bool = False) -> Result:
+    """Greedy (or, with ``optimal``, maximum-weight) matching and scores of
+    caller-given matrices (cf_match with X)."""
     L = B.lib()
     pairs_np = _pairs_np(pairs)
     P = len(pairs_np)
@@ -174,14 +205,78 @@ def match(pa: Pack, pb: Pack, pairs, X: torch.Tensor, *, ws: Workspace | None = 
     mt = torch.empty(int(m_off[-1]), dtype=torch.int32, device=dev)
     d_pairs = torch.from_numpy(pairs_np).to(dev)
     ws = ws or Workspace(dev)
-    prm = B.params()
+    prm = B.params(match_mode=B.CF_MATCH_OPTIMAL if optimal else B.CF_MATCH_GREEDY)
     wbuf = ws.get(ws_size(pa, pb, pairs_np, prm))
     X = X.contiguous()
     st = _stream_ptr(stream)
-    B.check(L.cf_match(pa.dev.data_ptr(), pb.dev.data_ptr(), d_pairs.data_ptr(), P, None, None, X.data_ptr(),
+    B.check(L.cf_match(pa.dev.data_ptr(), pb.dev.data_ptr(), d_pairs.data_ptr(), P, C.byref(prm), None, X.data_ptr(),
                        mt.data_ptr(), scores.data_ptr(), wbuf.data_ptr(), wbuf.numel(), st))
     B.check(L.cf_status_check(wbuf.data_ptr(), st))
     return Result(scores, mt, X, x_off, m_off)
+
+
+def distances(pa: Pack, pb: Pack, pairs, p: float = 3.0, *, scale01: bool = False, d_pairs=None,
+              out: torch.Tensor | None = None, stream=None, check_status: bool = True) -> torch.Tensor:
+    """The five Table 1 distances (Euclidean, Manhattan, Minkowski(p), Jaccard,
+    Cosine) of the resized transition matrices of every pair (cf_distances):
+    float32 [P, 5], min-max scaled to [0, 1] over the pairs with ``scale01``."""
+    L = B.lib()
+    pairs_np = _pairs_np(pairs)
+    P = len(pairs_np)
+    dev = pa.dev.device
+    if d_pairs is None:
+        d_pairs = torch.from_numpy(pairs_np).to(dev)
+    if out is None:
+        out = torch.empty(P, 5, dtype=torch.float32, device=dev)
+    n = C.c_size_t(0)
+    B.check(L.cf_distances_ws_size(P, C.byref(n)))
+    ws = torch.empty(max(int(n.value), 256), dtype=torch.uint8, device=dev)
+    st = _stream_ptr(stream)
+    B.check(L.cf_distances(pa.dev.data_ptr(), pb.dev.data_ptr(), d_pairs.data_ptr(), P, float(p),
+                           B.CF_DIST_SCALE01 if scale01 else 0, out.data_ptr(), ws.data_ptr(), ws.numel(), st))
+    if check_status:
+        B.check(L.cf_status_check(ws.data_ptr(), st))
+    return out
+
+
+def score_matrix(pairs, scores: torch.Tensor, n_rows: int, n_cols: int | None = None, *, symmetric: bool = True,
+                 d_pairs=None, stream=None) -> torch.Tensor:
+    """Dense [n_rows, n_cols] matrix of pair scores (cf_score_matrix)."""
+    L = B.lib()
+    pairs_np = _pairs_np(pairs)
+    dev = scores.device
+    n_cols = n_rows if n_cols is None else n_cols
+    if d_pairs is None:
+        d_pairs = torch.from_numpy(pairs_np).to(dev)
+    S = torch.empty(n_rows, n_cols, dtype=torch.float32, device=dev)
+    status = torch.empty(1, dtype=torch.int32, device=dev)
+    B.check(L.cf_score_matrix(d_pairs.data_ptr(), scores.contiguous().data_ptr(), len(pairs_np), n_rows, n_cols,
+                              int(symmetric), S.data_ptr(), status.data_ptr(), _stream_ptr(stream)))
+    bad = int(status.item())
+    if bad:
+        raise B.CfsimError(1, f"pair {bad - 1} is out of range")
+    return S
+
+
+def ward(points: torch.Tensor, stream=None):
+    """Ward linkage of the rows of ``points`` [n, dim] (cf_ward): returns
+    ``(merge [n-1, 2] int32, height [n-1] float32, size [n-1] int32)`` in
+    scipy's linkage convention."""
+    L = B.lib()
+    X = points.detach().to(torch.float32).contiguous()
+    n, dim = X.shape
+    dev = X.device
+    nb = C.c_size_t(0)
+    B.check(L.cf_ward_ws_size(n, C.byref(nb)))
+    ws = torch.empty(int(nb.value), dtype=torch.uint8, device=dev)
+    merge = torch.empty(max(n - 1, 0), 2, dtype=torch.int32, device=dev)
+    height = torch.empty(max(n - 1, 0), dtype=torch.float32, device=dev)
+    size = torch.empty(max(n - 1, 0), dtype=torch.int32, device=dev)
+    st = _stream_ptr(stream)
+    B.check(L.cf_ward(X.data_ptr(), n, dim, merge.data_ptr(), height.data_ptr(), size.data_ptr(), ws.data_ptr(),
+                      ws.numel(), st))
+    B.check(L.cf_status_check(ws.data_ptr(), st))
+    return merge, height, size
 
 
 def topk(scores: torch.Tensor, k: int, stream=None):
@@ -253,3 +348,71 @@ class CFSimilarity(torch.autograd.Function):
         omega, match = ctx.saved_tensors
         ga, gb, go = similarity_backward(ctx.pack_a, ctx.pack_b, ctx.pairs, omega, match, g, ctx.alpha, ctx.K)
         return ga, gb, go, None, None, None, None, None
+
+
+class Graph:
+    """A CUDA graph of cfsim calls (cf_graph_begin / cf_graph_end), replayed
+    with ``launch()``.
+
+    Capture runs on the graph's own stream::
+
+        g = Graph()
+        with g.capture():
+            similarity(..., d_pairs=..., out=..., ws=..., ws_bytes=..., check_status=False)
+        g.launch()
+
+    Everything the captured calls touch must already be allocated (pass
+    ``d_pairs``, ``out``, a sized ``ws`` and ``ws_bytes``), nothing in the
+    capture may block (``check_status=False``), and each kind of call must
+    have run once uncaptured before."""
+
+    def __init__(self, device="cuda"):
+        self.stream = torch.cuda.Stream(device=device)
+        self.handle = None
+
+    @contextlib.contextmanager
+    def capture(self):
+        L = B.lib()
+        if self.handle is not None:
+            raise RuntimeError("graph already captured")
+        cur = torch.cuda.current_stream()
+        self.stream.wait_stream(cur)
+        sp = int(self.stream.cuda_stream)
+        with torch.cuda.stream(self.stream):
+            B.check(L.cf_graph_begin(sp))
+            h = C.c_void_p(None)
+            try:
+                yield self
+            finally:
+                st = L.cf_graph_end(sp, C.byref(h))
+        B.check(st)
+        self.handle = h
+        cur.wait_stream(self.stream)
+
+    @property
+    def nodes(self) -> int:
+        return int(B.lib().cf_graph_nodes(self.handle))
+
+    def launch(self, stream=None) -> None:
+        B.check(B.lib().cf_graph_launch(self.handle, _stream_ptr(stream)))
+
+    def __del__(self):
+        if getattr(self, "handle", None) is not None:
+            try:
+                B.lib().cf_graph_destroy(self.handle)
+            except Exception:  # interpreter shutdown
+                pass
+            self.handle = None
+
+
+def probe(kind: int, reps: int = 3, stream=None) -> dict:
+    """On-chip peak of one kind (cf_probe): CF_PROBE_SMEM / L2 / DSMEM (bytes/s)
+    or CF_PROBE_FP32 (FLOP/s), with the SM clock of the fastest launch."""
+    L = B.lib()
+    n = C.c_size_t(0)
+    B.check(L.cf_probe_ws_size(int(kind), C.byref(n)))
+    ws = torch.empty(max(int(n.value), 256), dtype=torch.uint8, device="cuda")
+    r = B.cf_probe_result()
+    B.check(L.cf_probe(int(kind), ws.data_ptr(), ws.numel(), int(reps), _stream_ptr(stream), C.byref(r)))
+    return {"work": r.work, "best_ms": r.best_ms, "rate": r.rate, "sm_mhz": r.sm_mhz, "per_clk_sm": r.per_clk_sm,
+            "n_sm": r.n_sm}

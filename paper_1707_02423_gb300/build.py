@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcfsim.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["api.cu", "plan.cu", "forward.cu", "backward.cu", "misc.cu", "static_ws.cu"]
+SOURCES = ["api.cu", "plan.cu", "forward.cu", "backward.cu", "misc.cu", "static_ws.cu", "probe.cu", "graph.cu", "autotune.cu", "match_opt.cu", "distances.cu", "ward.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-I", INCLUDE,
          "-I", CSRC]

@@ -222,11 +222,13 @@ cf_status check_params(const cf_params* p) {
   if (p->K < 0 || p->K > 1000000) return fail(CF_ERR_INVALID_ARG, "K must be in [0, 1e6] (got %d)", p->K);
   if (p->norm_mode != CF_NORM_FROB && p->norm_mode != CF_NORM_NONE)
     return fail(CF_ERR_INVALID_ARG, "unknown norm_mode %d", p->norm_mode);
-  if (p->match_mode != CF_MATCH_GREEDY) return fail(CF_ERR_UNSUPPORTED, "unknown match_mode %d", p->match_mode);
+  if (p->match_mode != CF_MATCH_GREEDY && p->match_mode != CF_MATCH_OPTIMAL)
+    return fail(CF_ERR_INVALID_ARG, "unknown match_mode %d", p->match_mode);
   const uint32_t known = CF_FLAG_PER_PAIR_LAUNCH | CF_FLAG_PLAN_ONLY | CF_FLAG_REUSE_PLAN;
   if (p->flags & ~known) return fail(CF_ERR_INVALID_ARG, "unknown flags 0x%x", p->flags);
   if ((p->flags & CF_FLAG_PLAN_ONLY) && (p->flags & CF_FLAG_REUSE_PLAN))
     return fail(CF_ERR_INVALID_ARG, "CF_FLAG_PLAN_ONLY and CF_FLAG_REUSE_PLAN exclude each other");
+  if (p->tune < 0 || p->tune > kNumTunes) return fail(CF_ERR_INVALID_ARG, "tune must be in [0, %d] (got %d)", kNumTunes, p->tune);
   return CF_OK;
 }
 
@@ -262,7 +264,8 @@ cf_status scan_pairs(const void* h_pack_a, const void* h_pack_b, const int32_t* 
   const int32_t* eob = reinterpret_cast<const int32_t*>(static_cast<const char*>(h_pack_b) + hb.off_edge);
   int64_t xs = 0, ms = 0, ng = 0;
   size_t need = 0;
-  const ClassCfg cc = fwd_variant(0).cc;
+  // pairs that fit no single CTA: the global class, or the cluster class under a tune with clusters
+  const ClassCfg cc = fwd_class_cfg(0, kClassWarp, 0, 0);
   for (int p = 0; p < P; ++p) {
     const int a = h_pairs[2 * p], b = h_pairs[2 * p + 1];
     if (a < 0 || a >= ha.n_cfgs || b < 0 || b >= hb.n_cfgs)
@@ -282,15 +285,25 @@ cf_status scan_pairs(const void* h_pack_a, const void* h_pack_b, const int32_t* 
   return CF_OK;
 }
 
-// Forward kernel variant: CFSIM_FWD_VARIANT overrides the default (0).
-int active_variant() {
-  static int v = -1;
-  if (v < 0) {
-    const char* e = std::getenv("CFSIM_FWD_VARIANT");
-    v = (e && *e >= '0' && *e < '0' + num_fwd_variants()) ? *e - '0' : 0;
-  }
-  return v;
+}  // namespace
+
+namespace cfsim {
+// Kernel configuration of a tune id (cf_params.tune): 0 is the built-in
+// default (same as id 1); ids 1..kNumTunes enumerate variant x smallest group
+// level x matching policy x cluster size of the cluster tier.
+Tune decode_tune(int32_t id) {
+  static const int kClusters[4] = {0, 2, 4, 8};
+  const int idx = id >= 1 && id <= kNumTunes ? id - 1 : 0;
+  Tune t;
+  t.variant = idx % 2;
+  t.min_cls = kClassWarp - (idx / 2) % 3;
+  t.ranked = (idx / 6) % 3;
+  t.cluster = kClusters[idx / 18];
+  return t;
 }
+}  // namespace cfsim
+
+namespace {
 
 CallArgs base_args(const void* d_pack_a, const void* d_pack_b, const int32_t* d_pairs, int32_t P,
                    const cf_params* params, const float* d_omega, void* d_ws, size_t ws_bytes) {
@@ -299,6 +312,10 @@ CallArgs base_args(const void* d_pack_a, const void* d_pack_b, const int32_t* d_
   a.pack_b = d_pack_b;
   a.pairs = d_pairs;
   a.P = P;
+  const Tune tn = decode_tune(params ? params->tune : 0);
+  a.min_cls = tn.min_cls;
+  a.ranked = tn.ranked;
+  a.cluster = 0;
   if (params) {
     a.alpha = params->alpha;
     a.K = params->K;
@@ -345,7 +362,7 @@ const char* cf_status_string(cf_status s) {
 
 const char* cf_last_error_detail(void) { return g_err.c_str(); }
 
-int32_t cf_abi_version(void) { return 1; }
+int32_t cf_abi_version(void) { return 2; }
 
 cf_status cf_pack_size(const cf_cfg_view* cfgs, int32_t n_cfgs, int32_t F, size_t* bytes) {
   if (!bytes) return fail(CF_ERR_INVALID_ARG, "bytes is NULL");
@@ -438,11 +455,17 @@ cf_status cf_similarity(const void* d_pack_a, const void* d_pack_b, const int32_
   s = check_device_call(d_pack_a, d_pack_b, d_pairs, P, d_ws, ws_bytes);
   if (s) return s;
   if (!d_omega) return fail(CF_ERR_INVALID_ARG, "d_omega is NULL");
+  const bool optimal = params->match_mode == CF_MATCH_OPTIMAL && (d_scores || d_match);
+  if (optimal && !d_X)
+    return fail(CF_ERR_INVALID_ARG, "CF_MATCH_OPTIMAL runs on the matrices: d_X is required with d_scores / d_match");
   if (P == 0) return ok();
   CallArgs a = base_args(d_pack_a, d_pack_b, d_pairs, P, params, d_omega, d_ws, ws_bytes);
   a.X = d_X;
-  a.scores = d_scores;
-  a.match = d_match;
+  a.scores = optimal ? nullptr : d_scores;
+  a.match = optimal ? nullptr : d_match;
+  const Tune tn = decode_tune(params->tune);
+  // the cluster tier only in the batched form, and only where such clusters can be resident
+  if (!(params->flags & CF_FLAG_PER_PAIR_LAUNCH) && tn.cluster >= 2) a.cluster = cluster_supported(tn.variant, tn.cluster);
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e;
   if (params->flags & CF_FLAG_REUSE_PLAN) {
@@ -452,12 +475,23 @@ cf_status cf_similarity(const void* d_pack_a, const void* d_pack_b, const int32_
   } else {
     e = cudaMemsetAsync(d_ws, 0, sizeof(WsHeader), st);
     if (e != cudaSuccess) return cuda_fail(e, "workspace reset");
-    e = launch_plan(a, fwd_variant(active_variant()).cc, st);
+    e = launch_plan(a, fwd_class_cfg(tn.variant, a.min_cls, a.ranked, a.cluster), st);
     if (e != cudaSuccess) return cuda_fail(e, "plan launch");
   }
   if (!(params->flags & CF_FLAG_PLAN_ONLY)) {
-    e = launch_forward(a, active_variant(), (params->flags & CF_FLAG_PER_PAIR_LAUNCH) != 0, st);
+    e = launch_forward(a, tn.variant, (params->flags & CF_FLAG_PER_PAIR_LAUNCH) != 0, st);
     if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+    if (optimal) {
+      if (params->flags & CF_FLAG_REUSE_PLAN) {
+        e = cudaMemsetAsync(static_cast<char*>(d_ws) + offsetof(WsHeader, q_opt), 0, sizeof(uint32_t), st);
+        if (e != cudaSuccess) return cuda_fail(e, "queue reset");
+      }
+      a.X_in = d_X;
+      a.scores = d_scores;
+      a.match = d_match;
+      e = launch_match_optimal(a, st);
+      if (e != cudaSuccess) return cuda_fail(e, "optimal matching launch");
+    }
   }
   return ok();
 }
@@ -469,6 +503,8 @@ cf_status cf_match(const void* d_pack_a, const void* d_pack_b, const int32_t* d_
                                     d_ws, ws_bytes, stream);
   cf_status s = check_device_call(d_pack_a, d_pack_b, d_pairs, P, d_ws, ws_bytes);
   if (s) return s;
+  if (params && params->match_mode != CF_MATCH_GREEDY && params->match_mode != CF_MATCH_OPTIMAL)
+    return fail(CF_ERR_INVALID_ARG, "unknown match_mode %d", params->match_mode);
   if (P == 0) return ok();
   CallArgs a = base_args(d_pack_a, d_pack_b, d_pairs, P, nullptr, nullptr, d_ws, ws_bytes);
   a.X_in = d_X_in;
@@ -477,9 +513,12 @@ cf_status cf_match(const void* d_pack_a, const void* d_pack_b, const int32_t* d_
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaMemsetAsync(d_ws, 0, sizeof(WsHeader), st);
   if (e != cudaSuccess) return cuda_fail(e, "workspace reset");
-  e = launch_plan(a, fwd_variant(active_variant()).cc, st);
+  e = launch_plan(a, fwd_class_cfg(0, a.min_cls, a.ranked, 0), st);
   if (e != cudaSuccess) return cuda_fail(e, "plan launch");
-  e = launch_match_only(a, st);
+  if (params && params->match_mode == CF_MATCH_OPTIMAL)
+    e = launch_match_optimal(a, st);
+  else
+    e = launch_match_only(a, st);
   if (e != cudaSuccess) return cuda_fail(e, "match launch");
   return ok();
 }
@@ -536,7 +575,7 @@ cf_status cf_similarity_backward(const void* d_pack_a, const void* d_pack_b, con
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaMemsetAsync(d_ws, 0, sizeof(WsHeader), st);
   if (e != cudaSuccess) return cuda_fail(e, "workspace reset");
-  e = launch_plan(a, fwd_variant(active_variant()).cc, st);
+  e = launch_plan(a, fwd_class_cfg(0, a.min_cls, a.ranked, 0), st);
   if (e != cudaSuccess) return cuda_fail(e, "plan launch");
   e = launch_backward(a, st);
   if (e != cudaSuccess) return cuda_fail(e, "backward launch");

@@ -48,6 +48,7 @@ struct Ctx {
   size_t scratch_bytes;
   const float* om;  // omega, shared-memory copy
   int F, Fp;
+  int ranked;  // matching policy (ClassCfg::ranked)
 };
 
 // One pair, oriented: the row graph indexes rows of the resident matrix.
@@ -66,7 +67,7 @@ struct Geo {
   const float* c_attr;
 };
 
-__device__ __forceinline__ Geo make_geo(const Ctx& cx, int p, const ClassCfg& cc, int min_cls) {
+__device__ __forceinline__ Geo make_geo(const Ctx& cx, int p, const ClassCfg& cc) {
   Geo g;
   g.p = p;
   const int pa = __ldg(cx.pairs + 2 * p), pb = __ldg(cx.pairs + 2 * p + 1);
@@ -75,7 +76,7 @@ __device__ __forceinline__ Geo make_geo(const Ctx& cx, int p, const ClassCfg& cc
   g.nb = __ldg(cx.B.node_off + pb + 1) - bb;
   const int ea = __ldg(cx.A.edge_off + pa + 1) - __ldg(cx.A.edge_off + pa);
   const int eb = __ldg(cx.B.edge_off + pb + 1) - __ldg(cx.B.edge_off + pb);
-  g.s = classify(g.na, g.nb, ea, eb, cc, min_cls);
+  g.s = classify(g.na, g.nb, ea, eb, cc);
   const PackView& R = g.s.tr ? cx.B : cx.A;
   const PackView& C = g.s.tr ? cx.A : cx.B;
   const int rb = g.s.tr ? bb : ba, cbse = g.s.tr ? ba : bb;
@@ -173,8 +174,23 @@ __device__ __forceinline__ ColPad load_col(const int* cptr, const int2* cedge, i
   return c;
 }
 
-__device__ __forceinline__ float lds_at(const char* base, int byte_off) {
-  return *reinterpret_cast<const float*>(base + byte_off);
+// Loads of the iterate at byte offset a + b: from a generic pointer (shared
+// memory of this CTA, or global memory), or -- ClusterY -- from the
+// distributed shared memory of a thread-block cluster, where a holds a 32-bit
+// shared::cluster address (row u of the owning CTA's buffer 0) and the base
+// the offset of the buffer being read.
+struct ClusterY {
+  uint32_t b;
+};
+
+__device__ __forceinline__ float lds_at(const char* base, int a, int b) {
+  return *reinterpret_cast<const float*>(base + (a + b));
+}
+
+__device__ __forceinline__ float lds_at(ClusterY y, int a, int b) {
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(y.b + (uint32_t)a + (uint32_t)b));
+  return v;
 }
 
 // Entry (i, j) of  sum_{i->u} sum_{j->v} w_iu w_jv Y[u,v] + sum_{u->i} sum_{v->j} w_ui w_vj Y[u,v]
@@ -185,11 +201,12 @@ __device__ __forceinline__ float lds_at(const char* base, int byte_off) {
 // which covers every pair exactly once.  A = row i's first two out-neighbours
 // {u ld 4, w} (the sign bit of A.w flags further neighbours of i), Q = its
 // first two in-neighbours; padding entries carry weight 0.
-__device__ __forceinline__ float gather_fast(const char* Y, const int4 A, const int4 Q, const ColPad& c) {
-  const float a0 = lds_at(Y, A.x + c.vo0), a1 = lds_at(Y, A.x + c.vo1);
-  const float a2 = lds_at(Y, A.z + c.vo0), a3 = lds_at(Y, A.z + c.vo1);
-  const float b0 = lds_at(Y, Q.x + c.vi0), b1 = lds_at(Y, Q.x + c.vi1);
-  const float b2 = lds_at(Y, Q.z + c.vi0), b3 = lds_at(Y, Q.z + c.vi1);
+template <class YT>
+__device__ __forceinline__ float gather_fast(YT Y, const int4 A, const int4 Q, const ColPad& c) {
+  const float a0 = lds_at(Y, A.x, c.vo0), a1 = lds_at(Y, A.x, c.vo1);
+  const float a2 = lds_at(Y, A.z, c.vo0), a3 = lds_at(Y, A.z, c.vo1);
+  const float b0 = lds_at(Y, Q.x, c.vi0), b1 = lds_at(Y, Q.x, c.vi1);
+  const float b2 = lds_at(Y, Q.z, c.vi0), b3 = lds_at(Y, Q.z, c.vi1);
   const float so =
       fmaf(fabsf(__int_as_float(A.w)), fmaf(c.wo1, a3, c.wo0 * a2), __int_as_float(A.y) * fmaf(c.wo1, a1, c.wo0 * a0));
   const float si =
@@ -198,38 +215,40 @@ __device__ __forceinline__ float gather_fast(const char* Y, const int4 A, const 
 }
 
 // rr = row i's full out- and in-edge ranges into redge ({u ld 4, w}).
-__device__ __forceinline__ float row_extra(const char* Y, const int4 rr, const int2* redge, const ColPad& c) {
+template <class YT>
+__device__ __forceinline__ float row_extra(YT Y, const int4 rr, const int2* redge, const ColPad& c) {
   float s = 0.f;
   for (int k = rr.x + 2; k < rr.y; ++k) {
     const int2 e = redge[k];
-    s = fmaf(__int_as_float(e.y), fmaf(c.wo1, lds_at(Y, e.x + c.vo1), c.wo0 * lds_at(Y, e.x + c.vo0)), s);
+    s = fmaf(__int_as_float(e.y), fmaf(c.wo1, lds_at(Y, e.x, c.vo1), c.wo0 * lds_at(Y, e.x, c.vo0)), s);
   }
   for (int k = rr.z + 2; k < rr.w; ++k) {
     const int2 e = redge[k];
-    s = fmaf(__int_as_float(e.y), fmaf(c.wi1, lds_at(Y, e.x + c.vi1), c.wi0 * lds_at(Y, e.x + c.vi0)), s);
+    s = fmaf(__int_as_float(e.y), fmaf(c.wi1, lds_at(Y, e.x, c.vi1), c.wi0 * lds_at(Y, e.x, c.vi0)), s);
   }
   return s;
 }
 
 // cedge = the column graph's staged {v 4, w} entries (out-edges, then in-edges).
-__device__ __forceinline__ float col_extra(const char* Y, const int4 A, const int4 Q, const int4 rr,
-                                           const int2* redge, const int2* cedge, const ColPad& c) {
+template <class YT>
+__device__ __forceinline__ float col_extra(YT Y, const int4 A, const int4 Q, const int4 rr, const int2* redge,
+                                           const int2* cedge, const ColPad& c) {
   float s = 0.f;
   for (int f = c.xo0; f < c.xo1; ++f) {
     const int2 v = cedge[f];
-    float t = fmaf(fabsf(__int_as_float(A.w)), lds_at(Y, A.z + v.x), __int_as_float(A.y) * lds_at(Y, A.x + v.x));
+    float t = fmaf(fabsf(__int_as_float(A.w)), lds_at(Y, A.z, v.x), __int_as_float(A.y) * lds_at(Y, A.x, v.x));
     for (int k = rr.x + 2; k < rr.y; ++k) {
       const int2 e = redge[k];
-      t = fmaf(__int_as_float(e.y), lds_at(Y, e.x + v.x), t);
+      t = fmaf(__int_as_float(e.y), lds_at(Y, e.x, v.x), t);
     }
     s = fmaf(__int_as_float(v.y), t, s);
   }
   for (int f = c.xi0; f < c.xi1; ++f) {
     const int2 v = cedge[f];
-    float t = fmaf(__int_as_float(Q.w), lds_at(Y, Q.z + v.x), __int_as_float(Q.y) * lds_at(Y, Q.x + v.x));
+    float t = fmaf(__int_as_float(Q.w), lds_at(Y, Q.z, v.x), __int_as_float(Q.y) * lds_at(Y, Q.x, v.x));
     for (int k = rr.z + 2; k < rr.w; ++k) {
       const int2 e = redge[k];
-      t = fmaf(__int_as_float(e.y), lds_at(Y, e.x + v.x), t);
+      t = fmaf(__int_as_float(e.y), lds_at(Y, e.x, v.x), t);
     }
     s = fmaf(__int_as_float(v.y), t, s);
   }
@@ -597,7 +616,8 @@ __device__ __forceinline__ void run_pair_s(const Ctx& cx, const Geo& g, const Gr
   if (cx.X) store_x(grp, cx, g, Xs, ld);
   if (cx.scores || cx.match) {
     int32_t* mo = cx.match ? cx.match + cx.m_off[g.p] : nullptr;
-    if (5 * (size_t)(s.n_row + s.n_col) + 16 <= 4 * (size_t)nn) {  // room for the ranked lists' state
+    const bool ranked = cx.ranked == 0 || (cx.ranked == 1 && grp.bar != 0);  // bar 0: the whole CTA
+    if (ranked && 5 * (size_t)(s.n_row + s.n_col) + 16 <= 4 * (size_t)nn) {  // room for the ranked lists' state
       const float sc = greedy_ranked(grp, Xs, ld, s.n_row, s.n_col, s.tr, reinterpret_cast<int16_t*>(ehb),
                                      reinterpret_cast<int16_t*>(ehb) + s.n_row * s.n_col,
                                      reinterpret_cast<unsigned char*>(freeb), mo, cx.hdr, g.p);
@@ -785,6 +805,7 @@ __device__ __forceinline__ bool make_ctx(const CallArgs& a, float* s_om, Ctx& cx
     cx.match = a.match;
     cx.F = cx.A.F;
     cx.Fp = cx.A.F_pad;
+    cx.ranked = a.ranked;
     cx.om = s_om;
     *s_ok = (cx.A.F == cx.B.F && cx.A.F_pad == cx.B.F_pad) ? 1 : 0;
     if (!*s_ok && blockIdx.x == 0) set_status(cx.hdr, 1 /* CF_ERR_INVALID_ARG */, -1);
@@ -804,8 +825,8 @@ __device__ __forceinline__ bool make_ctx(const CallArgs& a, float* s_om, Ctx& cx
 // dynamic shared memory split 1 / 4 / (NT/32) ways for the three group levels.
 constexpr size_t kFwdSmem = 225280;
 template <int NT>
-__host__ __device__ constexpr ClassCfg fwd_cfg() {
-  return ClassCfg{NT, (int)kFwdSmem, (int)kFwdSmem / 4, (int)kFwdSmem / (NT / 32)};
+__host__ __device__ constexpr ClassCfg fwd_cfg(int min_cls = kClassWarp, int ranked = 0, int cluster = 0) {
+  return ClassCfg{NT, (int)kFwdSmem, (int)kFwdSmem / 4, (int)kFwdSmem / (NT / 32), min_cls, ranked, cluster};
 }
 
 template <int NT>
@@ -819,10 +840,11 @@ __global__ void __launch_bounds__(NT, 1) fwd_batched_kernel(CallArgs a, int per_
   __shared__ int s_redi[5][64];
   if (!make_ctx(a, s_om, s_cx, &s_ok)) return;
   const Ctx& cx = s_cx;
-  const ClassCfg cc = fwd_cfg<NT>();
+  const bool single = per_pair >= 0;  // the plain form: one launch runs exactly one pair on the whole CTA
+  // the per-pair form keeps every pair on the whole CTA
+  const ClassCfg cc = fwd_cfg<NT>(single ? (int)kClassCta : a.min_cls, a.ranked);
   const int t = threadIdx.x;
   const Group cta{t, NT, 0, s_redf[0], s_redi[0]};
-  const bool single = per_pair >= 0;  // the plain form: one launch runs exactly one pair on the whole CTA
 
   uint32_t n[kNumClasses];
   for (int c = 0; c < kNumClasses; ++c) n[c] = single ? 0u : cx.hdr->n_class[c];
@@ -841,7 +863,7 @@ __global__ void __launch_bounds__(NT, 1) fwd_batched_kernel(CallArgs a, int per_
         __syncthreads();
         if (q >= n[kClassGlobal]) break;
         {
-          const Geo g = make_geo(cx, (int)cx.queue[q], cc, kClassWarp);
+          const Geo g = make_geo(cx, (int)cx.queue[q], cc);
           if (staged_fits(g, cc.z_cta))
             run_pair_g<true>(cx, g, cta, slot, smem);
           else
@@ -855,7 +877,7 @@ __global__ void __launch_bounds__(NT, 1) fwd_batched_kernel(CallArgs a, int per_
   // is a sub-partition of the previous one's region, and every group ends a
   // pair with its own barrier, so no CTA-wide barrier sits between levels.
   uint32_t qbase = n[kClassGlobal];
-  for (int level = kClassCta; level <= (single ? kClassCta : kClassWarp); ++level) {
+  for (int level = kClassCta; level <= cc.min_cls; ++level) {
     Group grp = cta;
     unsigned char* region = smem;
     int slot = 0;
@@ -877,7 +899,7 @@ __global__ void __launch_bounds__(NT, 1) fwd_batched_kernel(CallArgs a, int per_
       grp.sync();
       if (q >= count) break;
       if (single && grp.rank == 0) s_p[slot] = 1u;  // the next pull ends the loop
-      const Geo g = make_geo(cx, single ? per_pair : (int)cx.queue[qbase + q], cc, single ? kClassCta : kClassWarp);
+      const Geo g = make_geo(cx, single ? per_pair : (int)cx.queue[qbase + q], cc);
       if (g.s.cls == kClassGlobal) {  // only in the plain form: scratch slot 0
         if (global_slot_bytes(g.na, g.nb) > cx.scratch_bytes) {
           if (t == 0) set_status(cx.hdr, 2 /* CF_ERR_WORKSPACE */, per_pair);
@@ -893,6 +915,265 @@ __global__ void __launch_bounds__(NT, 1) fwd_batched_kernel(CallArgs a, int per_
       if (single) break;
     }
     qbase += single ? 0u : n[level];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The cluster tier: a pair too large for one CTA's shared memory is split by
+// rows over the C CTAs of a thread-block cluster.  CTA r holds rows
+// [r S, r S + S) (S = ceil(n_row / C)) of (1 - alpha) Ehat and of both
+// iterates, the first-two / further neighbour lists of its rows, and the
+// whole column graph.  The row lists name each neighbour row u by the 32-bit
+// shared::cluster address of row u in its owner's buffer 0, so a gather
+// reads the owner's shared memory directly (ld.shared::cluster): one code
+// path for local and remote rows.  One cluster barrier per iteration (inside
+// the cluster-wide norm reduction) separates the reads of Y_k from the
+// writes of Y_{k+2} into the same buffer.  X_K is then written to the
+// cluster's scratch slot and CTA 0 runs the greedy matching on it.
+
+__device__ __forceinline__ uint32_t cl_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cl_size() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cl_index() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+// shared::cluster address of the same shared-memory location in CTA `rank`
+__device__ __forceinline__ uint32_t cl_map(const void* p, uint32_t rank) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+// All threads of all CTAs of the cluster; release / acquire at cluster scope.
+// The CTAs of a cluster are co-scheduled, so every arrival happens.
+__device__ __forceinline__ void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ float cl_ld_f32(uint32_t addr) {
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t cl_ld_u32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+// Shared state of the cluster kernel besides the pair region.
+struct ClState {
+  float part[2];       // this CTA's partial sum, two parities
+  float redw[64];      // per-warp partials, two parities
+  uint32_t q;          // the pair index CTA 0 pulled
+  uint32_t rbase[kMaxCluster];  // cluster address of each CTA's region
+  uint32_t paddr[kMaxCluster];  // cluster address of each CTA's part[]
+  uint32_t qaddr;               // cluster address of CTA 0's q
+};
+
+// Sum of v over every thread of the cluster, the same bits on every thread:
+// warps -> CTA (one CTA barrier) -> cluster (one cluster barrier; lane r
+// reads CTA r's partial).
+__device__ __forceinline__ float cl_sum(float v, int par, ClState& st, int C) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, NW = blockDim.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) st.redw[par * 32 + w] = v;
+  __syncthreads();
+  if (w == 0) {
+    const float x = warp_sum(lane < NW ? st.redw[par * 32 + lane] : 0.f);
+    if (lane == 0) st.part[par] = x;
+  }
+  cl_sync();
+  return warp_sum(lane < C ? cl_ld_f32(st.paddr[lane] + 4u * par) : 0.f);
+}
+
+__device__ __noinline__ void run_pair_c(const Ctx& cx, const Geo& g, const Group& grp, int C, int rank, float* slot,
+                                        unsigned char* region, ClState& st) {
+  const Shape& s = g.s;
+  const int t = grp.rank, G = grp.size;
+  const int ld = s.ld;
+  const int slab = ceil_div(s.n_row, C);
+  const int i0 = rank * slab;
+  const int rows = max(0, min(s.n_row, i0 + slab) - i0);
+  const int nn = slab * ld;
+  float* ehb = reinterpret_cast<float*>(region);
+  float* buf0 = ehb + nn;
+  float* buf1 = buf0 + nn;
+  int4* ra = reinterpret_cast<int4*>(region + align_up(12 * (size_t)nn, 16));
+  int4* rq = ra + slab;
+  int4* rr = rq + slab;
+  int2* redge = reinterpret_cast<int2*>(rr + slab);
+  // cluster address of row u (of the whole row graph) in its owner's buffer 0
+  auto caddr = [&](int u) -> int {
+    const int o = u / slab;
+    return (int)(st.rbase[o] + 4u * (uint32_t)nn + 4u * (uint32_t)((u - o * slab) * ld));
+  };
+
+  const int eo0 = __ldg(g.r_optr), ei0 = __ldg(g.r_iptr);
+  const int so0 = __ldg(g.r_optr + i0) - eo0, so1 = __ldg(g.r_optr + i0 + rows) - eo0;
+  const int si0 = __ldg(g.r_iptr + i0) - ei0, si1 = __ldg(g.r_iptr + i0 + rows) - ei0;
+  const int n_so = so1 - so0, n_si = si1 - si0;
+  const int co0 = __ldg(g.c_optr), ci0 = __ldg(g.c_iptr);
+  const int e_col = __ldg(g.c_optr + s.n_col) - co0;
+  int2* cedge = redge + (n_so + n_si);
+  int* cptr = reinterpret_cast<int*>(cedge + 2 * e_col);
+  for (int k = t; k < e_col; k += G) {
+    const CfAdj a = ldg_adj(g.c_oadj + co0 + k), b = ldg_adj(g.c_iadj + ci0 + k);
+    cedge[k] = make_int2(4 * a.nbr, __float_as_int(a.w));
+    cedge[e_col + k] = make_int2(4 * b.nbr, __float_as_int(b.w));
+  }
+  for (int k = t; k <= s.n_col; k += G) {
+    cptr[k] = __ldg(g.c_optr + k) - co0;
+    cptr[s.n_col + 1 + k] = e_col + __ldg(g.c_iptr + k) - ci0;
+  }
+  for (int lr = t; lr < rows; lr += G) {
+    const int i = i0 + lr;
+    const int o0 = __ldg(g.r_optr + i) - eo0, o1 = __ldg(g.r_optr + i + 1) - eo0;
+    const int q0 = __ldg(g.r_iptr + i) - ei0, q1 = __ldg(g.r_iptr + i + 1) - ei0;
+    const CfAdj z{0, 0.f};
+    const CfAdj a0 = o1 > o0 ? ldg_adj(g.r_oadj + eo0 + o0) : z, a1 = o1 > o0 + 1 ? ldg_adj(g.r_oadj + eo0 + o0 + 1) : z;
+    const CfAdj b0 = q1 > q0 ? ldg_adj(g.r_iadj + ei0 + q0) : z, b1 = q1 > q0 + 1 ? ldg_adj(g.r_iadj + ei0 + q0 + 1) : z;
+    const int flag = (o1 - o0 > 2 || q1 - q0 > 2) ? (int)0x80000000 : 0;
+    ra[lr] = make_int4(caddr(a0.nbr), __float_as_int(a0.w), caddr(a1.nbr), __float_as_int(a1.w) | flag);
+    rq[lr] = make_int4(caddr(b0.nbr), __float_as_int(b0.w), caddr(b1.nbr), __float_as_int(b1.w));
+    rr[lr] = make_int4(o0 - so0, o1 - so0, n_so + q0 - si0, n_so + q1 - si0);
+  }
+  for (int k = t; k < n_so; k += G) {
+    const CfAdj a = ldg_adj(g.r_oadj + eo0 + so0 + k);
+    redge[k] = make_int2(caddr(a.nbr), __float_as_int(a.w));
+  }
+  for (int k = t; k < n_si; k += G) {
+    const CfAdj b = ldg_adj(g.r_iadj + ei0 + si0 + k);
+    redge[n_so + k] = make_int2(caddr(b.nbr), __float_as_int(b.w));
+  }
+  for (int lr = t; lr < rows; lr += G) buf1[lr] = attr_norm(g.r_attr + (size_t)(i0 + lr) * cx.Fp, cx.om, cx.Fp);
+  const bool act = t < s.R * s.n_col;
+  const int j = act ? t % s.n_col : 0;
+  const int r0 = act ? t / s.n_col : 0;
+  const int Mt = (act && rows > r0) ? ceil_div(rows - r0, s.R) : 0;
+  const int step = s.R * ld;
+  const int off0 = r0 * ld + j;
+  const float* bcol = g.c_attr + (size_t)j * cx.Fp;
+  const float cj = attr_norm(bcol, cx.om, cx.Fp);
+  __syncthreads();
+
+  // a3: E over the slab, |E|_F over the cluster, Ehat = X_0
+  float ss = 0.f;
+  for (int m = 0, lr = r0, off = off0; m < Mt; ++m, lr += s.R, off += step) {
+    const float dot = attr_dot(g.r_attr + (size_t)(i0 + lr) * cx.Fp, bcol, cx.om, cx.Fp);
+    const float den = buf1[lr] * cj;
+    const float e = den > 0.f ? dot / den : 0.f;
+    ehb[off] = e;
+    ss = fmaf(e, e, ss);
+  }
+  const float tot = cl_sum(ss, 0, st, C);
+  const float inv = tot > 0.f ? 1.0f / sqrtf(tot) : 0.f;
+  const float uni = 1.0f / sqrtf((float)s.n_row * (float)s.n_col);
+  const float cb = 1.f - cx.alpha;
+  for (int m = 0, off = off0; m < Mt; ++m, off += step) {
+    const float eh = tot > 0.f ? ehb[off] * inv : uni;
+    buf0[off] = eh;
+    ehb[off] = cb * eh;
+  }
+  cl_sync();  // every slab of Y_0 (and the staged lists) visible
+  const ColPad cl = load_col(cptr, cedge, s.n_col, j);
+
+  // a4: K renormalised iterations, one cluster barrier each
+  float sk = 1.f;
+  for (int k = 0; k < cx.K; ++k) {
+    const ClusterY cur{(k & 1) ? 4u * (uint32_t)nn : 0u};
+    float* nxt = (k & 1) ? buf0 : buf1;
+    const float ca = 0.5f * cx.alpha * sk;
+    ss = 0.f;
+    for (int m = 0, lr = r0, off = off0; m < Mt; ++m, lr += s.R, off += step) {
+      const int4 A = ra[lr], Q = rq[lr];
+      float z = gather_fast(cur, A, Q, cl);
+      if (A.w < 0 || cl.flag) {
+        const int4 R4 = rr[lr];
+        if (A.w < 0) z += row_extra(cur, R4, redge, cl);
+        if (cl.flag) z += col_extra(cur, A, Q, R4, redge, cedge, cl);
+      }
+      const float y = fmaf(ca, z, ehb[off]);
+      nxt[off] = y;
+      ss = fmaf(y, y, ss);
+    }
+    const float yy = cl_sum(ss, (k + 1) & 1, st, C);
+    sk = cx.norm_mode == 0 ? 1.0f / sqrtf(yy) : 1.f;
+  }
+  const float* Xs = (cx.K & 1) ? buf1 : buf0;
+
+  // X_K to the scratch slot (row-graph orientation, stride n_col) and, if
+  // asked, to the caller's n_a x n_b output
+  float* xo = cx.X ? cx.X + cx.x_off[g.p] : nullptr;
+  for (int m = 0, lr = r0, off = off0; m < Mt; ++m, lr += s.R, off += step) {
+    const float x = Xs[off] * sk;
+    const int i = i0 + lr;
+    slot[(size_t)i * s.n_col + j] = x;
+    if (xo) xo[s.tr ? (size_t)j * s.n_row + i : (size_t)i * s.n_col + j] = x;
+  }
+  cl_sync();  // the whole X_K is in the slot
+  if (rank == 0 && (cx.scores || cx.match)) {
+    int32_t* ms = reinterpret_cast<int32_t*>(slot + (size_t)s.n_row * s.n_col);
+    int32_t* mo = cx.match ? cx.match + cx.m_off[g.p] : nullptr;
+    const float sc = greedy<int32_t>(grp, slot, s.n_col, s.n_row, s.n_col, s.tr, ms, ms + s.n_row, mo, cx.hdr, g.p);
+    if (cx.scores && t == 0) cx.scores[g.p] = sc;
+  }
+}
+
+// Persistent clusters drain the cluster-class queue (after the global and
+// shared-memory classes in the plan's queue): CTA 0 of a cluster pulls a
+// pair and every CTA reads the index from its shared memory.  Each cluster
+// uses the scratch slot of its index.
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) fwd_cluster_kernel(CallArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(16) float s_om[kMaxF];
+  __shared__ Ctx s_cx;
+  __shared__ int s_ok;
+  __shared__ ClState st;
+  __shared__ float s_redf[64];
+  __shared__ int s_redi[64];
+  if (!make_ctx(a, s_om, s_cx, &s_ok)) return;  // same outcome on every CTA (depends on the packs only)
+  const Ctx& cx = s_cx;
+  const int t = threadIdx.x;
+  const int C = (int)cl_size(), rank = (int)cl_rank();
+  const uint32_t cid = cl_index();
+  const uint32_t n_cl = cx.hdr->n_class[kClassCluster];
+  if (n_cl == 0) return;
+  const uint64_t need = cx.hdr->slot_need;
+  const uint64_t nslots = need ? cx.scratch_bytes / need : 0;
+  if (nslots == 0) {
+    if (cid == 0 && rank == 0 && t == 0) set_status(cx.hdr, 2 /* CF_ERR_WORKSPACE */, -1);
+    return;
+  }
+  if (cid >= nslots) return;  // the whole cluster
+  const ClassCfg cc = fwd_cfg<NT>(a.min_cls, a.ranked, C);
+  uint32_t qbase = 0;
+  for (int c = 0; c < kClassCluster; ++c) qbase += cx.hdr->n_class[c];
+  if (t < C) {
+    st.rbase[t] = cl_map(smem, t);
+    st.paddr[t] = cl_map(st.part, t);
+  }
+  if (t == 0) st.qaddr = cl_map(&st.q, 0);
+  __syncthreads();
+  float* slot = reinterpret_cast<float*>(cx.scratch + (size_t)cid * need);
+  const Group cta{t, NT, 0, s_redf, s_redi};
+  for (;;) {
+    if (rank == 0 && t == 0) st.q = atomicAdd(&cx.hdr->q_next[kClassCluster], 1u);
+    cl_sync();
+    const uint32_t q = cl_ld_u32(st.qaddr);
+    cl_sync();  // CTA 0 overwrites q only after every CTA has read it
+    if (q >= n_cl) break;
+    const Geo g = make_geo(cx, (int)cx.queue[qbase + q], cc);
+    run_pair_c(cx, g, cta, C, rank, slot, smem, st);
   }
 }
 
@@ -955,17 +1236,89 @@ cudaError_t launch_fwd(const CallArgs& a, bool per_pair, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int NT>
+struct ClusterInit {
+  bool done = false;
+  int n_clusters[kMaxCluster + 1] = {};  // resident clusters per size, -1 unknown
+};
+
+template <int NT>
+ClusterInit<NT>& cluster_init() {
+  static ClusterInit<NT> ci;
+  if (!ci.done) {
+    for (int c = 0; c <= kMaxCluster; ++c) ci.n_clusters[c] = -1;
+    ci.done = true;
+  }
+  return ci;
+}
+
+template <int NT>
+int resident_clusters(int C) {
+  ClusterInit<NT>& ci = cluster_init<NT>();
+  if (C < 2 || C > kMaxCluster) return 0;
+  if (ci.n_clusters[C] >= 0) return ci.n_clusters[C];
+  int n = 0;
+  if (cudaFuncSetAttribute(fwd_cluster_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem) ==
+          cudaSuccess &&
+      cudaFuncSetAttribute(fwd_cluster_kernel<NT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(NT, 1, 1);
+    cfg.dynamicSmemBytes = kFwdSmem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaOccupancyMaxActiveClusters(&n, fwd_cluster_kernel<NT>, &cfg) != cudaSuccess) n = 0;
+  }
+  cudaGetLastError();
+  ci.n_clusters[C] = n;
+  return n;
+}
+
+template <int NT>
+cudaError_t launch_cluster(const CallArgs& a, cudaStream_t s) {
+  const int C = a.cluster;
+  const int n = resident_clusters<NT>(C);
+  if (n <= 0) return cudaErrorInvalidConfiguration;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(n * C, 1, 1);
+  cfg.blockDim = dim3(NT, 1, 1);
+  cfg.dynamicSmemBytes = kFwdSmem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fwd_cluster_kernel<NT>, a);
+}
+
 }  // namespace
+
+int cluster_supported(int v, int C) {
+  const int n = v == 1 ? resident_clusters<512>(C) : resident_clusters<1024>(C);
+  return n > 0 ? C : 0;
+}
 
 // Variants of the persistent forward kernel: 0 = 1024 threads (64 registers,
 // 32 warps per SM), 1 = 512 threads (128 registers, 16 warps per SM).
 int num_fwd_variants() { return 2; }
 
-FwdVariant fwd_variant(int v) {
-  return v == 1 ? FwdVariant{512, 0, 1, fwd_cfg<512>()} : FwdVariant{1024, 0, 1, fwd_cfg<1024>()};
+ClassCfg fwd_class_cfg(int v, int min_cls, int ranked, int cluster) {
+  return v == 1 ? fwd_cfg<512>(min_cls, ranked, cluster) : fwd_cfg<1024>(min_cls, ranked, cluster);
 }
 
 cudaError_t launch_forward(const CallArgs& a, int variant, bool per_pair, cudaStream_t s) {
+  if (!per_pair && a.cluster >= 2) {  // the cluster tier first: its pairs are the largest
+    const cudaError_t e = variant == 1 ? launch_cluster<512>(a, s) : launch_cluster<1024>(a, s);
+    if (e != cudaSuccess) return e;
+  }
   return variant == 1 ? launch_fwd<512>(a, per_pair, s) : launch_fwd<1024>(a, per_pair, s);
 }
 

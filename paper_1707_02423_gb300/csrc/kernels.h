@@ -31,15 +31,26 @@ struct CallArgs {
   float* grad_w_a;
   float* grad_w_b;
   float* grad_omega;
+  // kernel configuration (the tune of cf_params)
+  int min_cls;  // smallest group level of the batched forward
+  int ranked;   // matching policy of resident pairs (ClassCfg::ranked)
+  int cluster;  // CTAs per cluster of the cluster tier, 0 = none
 };
 
-// Batched forward kernel variants (threads per CTA, rows per thread).
-struct FwdVariant {
-  int nt, reserved, min_blocks;
-  ClassCfg cc;
-};
+// Batched forward kernel variants: 0 = 1024 threads per CTA, 1 = 512.
 int num_fwd_variants();
-FwdVariant fwd_variant(int v);
+// Class configuration of variant v with the given smallest group level,
+// matching policy and cluster size.
+ClassCfg fwd_class_cfg(int v, int min_cls, int ranked, int cluster);
+// C if clusters of C CTAs of variant v can be resident on this device, else 0.
+int cluster_supported(int v, int C);
+
+// Kernel configuration selected by cf_params.tune (see decode_tune).
+constexpr int kNumTunes = 72;
+struct Tune {
+  int variant, min_cls, ranked, cluster;
+};
+Tune decode_tune(int32_t id);
 
 // a7: device-side plan: validate pairs, classify, cost-order them into the
 // queue, and compute the X / match offsets.
@@ -51,12 +62,25 @@ cudaError_t launch_forward(const CallArgs& a, int variant, bool per_pair, cudaSt
 // Greedy matching + score on caller-given matrices.
 cudaError_t launch_match_only(const CallArgs& a, cudaStream_t s);
 
+// Maximum-weight assignment + score on the matrices a.X_in (the plan must have
+// run); CFGs of up to opt_max_blocks() blocks.
+cudaError_t launch_match_optimal(const CallArgs& a, cudaStream_t s);
+int opt_max_blocks();
+
 // Pack weight update from user-order weights (pointers into a device pack).
 cudaError_t launch_set_weights(CfAdj* out_adj, CfAdj* in_adj, const int32_t* in_eid, const int32_t* u2c,
                                int64_t n_user_edges, int64_t n_edges, const float* w_user, cudaStream_t s);
 
 // a8: adjoint (workspace layout bwd_layout; the plan must have run).
 cudaError_t launch_backward(const CallArgs& a, cudaStream_t s);
+
+// The element-wise Table 1 distances of resized transition matrices
+// (workspace dist_ws_bytes(); CFGs up to dist_max_blocks() blocks).
+constexpr int kNumDist = 5;
+size_t dist_ws_bytes();
+int dist_max_blocks();
+cudaError_t launch_distances(const void* pack_a, const void* pack_b, const int32_t* pairs, int P, float p, bool scale,
+                             float* out, void* ws, cudaStream_t s);
 
 // Top-k per row.
 cudaError_t launch_topk(const float* scores, int Q, int C, int k, float* top, int32_t* idx, cudaStream_t s);

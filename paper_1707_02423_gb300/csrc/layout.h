@@ -48,27 +48,34 @@ struct PackHeader {
   int64_t off_attr;     // float [n_blocks * F_pad]
 };
 
-// Execution classes of a pair, in queue order (largest work first): the
-// global-memory tier, then the three shared-memory group levels of the
-// persistent kernel (whole CTA, quarter CTA, single warp).
+// Execution classes of a pair, in queue order: the global-memory tier, the
+// three shared-memory group levels of the persistent kernel (whole CTA,
+// quarter CTA, single warp), and the cluster tier (rows split over the CTAs
+// of a thread-block cluster, iterate in distributed shared memory).
 enum PairClass : int {
   kClassGlobal = 0,
   kClassCta = 1,
   kClassQuarter = 2,
   kClassWarp = 3,
-  kNumClasses = 4,
-  kClassSkip = 4
+  kClassCluster = 4,
+  kNumClasses = 5,
+  kClassSkip = 5
 };
+constexpr int kMaxCluster = 16;
 constexpr int kBuckets = 64;  // cost buckets per class (two per octave)
 
 // Shape of the batched forward kernel: threads per CTA and the shared-memory
 // region (bytes) a pair may use at each group level.  The plan and the kernel
 // classify pairs with the same values.
 struct ClassCfg {
-  int nt;     // threads per CTA (the CTA-level group)
-  int z_cta;  // region of the CTA-level group
-  int z_qtr;  // region of each of the four quarter groups (nt / 4 threads)
-  int z_wrp;  // region of each warp
+  int nt;       // threads per CTA (the CTA-level group)
+  int z_cta;    // region of the CTA-level group
+  int z_qtr;    // region of each of the four quarter groups (nt / 4 threads)
+  int z_wrp;    // region of each warp
+  int min_cls;  // smallest group level pairs may go to (kClassWarp: all levels)
+  int ranked;   // matching of resident pairs: 0 ranked lists wherever their
+                // state fits, 1 only below the whole-CTA level, 2 never (rescans)
+  int cluster;  // CTAs per cluster of the cluster tier (0: no cluster tier)
 };
 
 // How a pair maps onto a group of G threads.  The "row" graph indexes the
@@ -107,12 +114,11 @@ CF_HD size_t group_region(int cls, const ClassCfg& c) {
   return (size_t)(cls == kClassWarp ? c.z_wrp : cls == kClassQuarter ? c.z_qtr : c.z_cta);
 }
 
-// Smallest group level whose region holds the pair, with the orientation of
-// fewest rows per thread (ties: untransposed).  min_cls limits the levels
-// tried (kClassCta: the whole CTA only).
-CF_HD Shape classify(int na, int nb, int ea, int eb, const ClassCfg& c, int min_cls = kClassWarp) {
+// Smallest group level (not below c.min_cls) whose region holds the pair,
+// with the orientation of fewest rows per thread (ties: untransposed).
+CF_HD Shape classify(int na, int nb, int ea, int eb, const ClassCfg& c) {
   Shape s{};
-  for (int cls = min_cls; cls >= kClassCta; --cls) {
+  for (int cls = c.min_cls; cls >= kClassCta; --cls) {
     const int G = group_size(cls, c);
     const size_t Z = group_region(cls, c);
     int R0 = 0, M0 = 0, R1 = 0, M1 = 0;
@@ -125,6 +131,27 @@ CF_HD Shape classify(int na, int nb, int ea, int eb, const ClassCfg& c, int min_
       s.n_row = tr ? nb : na;
       s.n_col = tr ? na : nb;
       s.R = tr ? R1 : R0;
+      s.M = tr ? M1 : M0;
+      s.ld = pair_ld(s.n_col);
+      return s;
+    }
+  }
+  if (c.cluster >= 2) {
+    // rows in c.cluster slabs, one per CTA; each CTA holds its slab of the
+    // three matrices, its slab's row lists and the whole column graph
+    int M0 = 0, M1 = 0;
+    const int s0 = ceil_div(na, c.cluster), s1 = ceil_div(nb, c.cluster);
+    const bool f0 = nb <= c.nt && resident_bytes(s0, pair_ld(nb), ea, nb, eb) <= (size_t)c.z_cta;
+    const bool f1 = na <= c.nt && resident_bytes(s1, pair_ld(na), eb, na, ea) <= (size_t)c.z_cta;
+    if (f0) M0 = ceil_div(s0, c.nt / nb);
+    if (f1) M1 = ceil_div(s1, c.nt / na);
+    if (f0 || f1) {
+      const bool tr = !f0 || (f1 && M1 < M0);
+      s.cls = kClassCluster;
+      s.tr = tr ? 1 : 0;
+      s.n_row = tr ? nb : na;
+      s.n_col = tr ? na : nb;
+      s.R = c.nt / s.n_col;
       s.M = tr ? M1 : M0;
       s.ld = pair_ld(s.n_col);
       return s;
@@ -190,7 +217,7 @@ struct WsHeader {
   uint64_t slot_need;      // bytes of scratch the largest global-class pair needs
   uint64_t bwd_slot_need;  // bytes of adjoint scratch the largest pair needs
   uint32_t q_bwd;          // adjoint work counter
-  uint32_t pad_;
+  uint32_t q_opt;          // optimal-matching work counter
   uint32_t hist[kNumClasses][kBuckets];
   uint32_t cursor[kNumClasses][kBuckets];
   int64_t x_total, m_total;

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_count_kernel(CallArgs a, Cl
       set_status(c.hdr, 1 /* CF_ERR_INVALID_ARG */, p);
     } else {
       atomicAdd(&c.hdr->hist[f.cls][f.bucket], 1u);
-      if (f.cls == kClassGlobal)
+      if (f.cls == kClassGlobal || f.cls == kClassCluster)  // both use a scratch slot
         atomicMax(reinterpret_cast<unsigned long long*>(&c.hdr->slot_need),
                   (unsigned long long)global_slot_bytes(f.na, f.nb));
       atomicMax(reinterpret_cast<unsigned long long*>(&c.hdr->bwd_slot_need),

@@ -35,7 +35,7 @@ def test_every_declared_symbol_is_exported(L):
     for n in names:
         assert hasattr(L, n), n
     assert set(names) == set(B.SIGNATURES), set(names) ^ set(B.SIGNATURES)
-    assert L.cf_abi_version() == 1
+    assert L.cf_abi_version() == 2
     for s in range(7):
         assert L.cf_status_string(s)
 
@@ -178,3 +178,16 @@ def test_sizes_and_argument_checks(L):
     assert L.cf_similarity(None, dummy, dummy, 3, C.byref(prm), dummy, None, None, None, dummy, 1 << 20, None) == 1
     assert L.cf_similarity(dummy, dummy, dummy, 3, C.byref(prm), dummy, None, None, None, dummy, 16, None) == 2
     assert L.cf_topk(dummy, 2, 10, 11, dummy, dummy, None) == 1
+
+
+def test_graph_and_probe_argument_checks(L):
+    h = C.c_void_p(None)
+    assert L.cf_graph_begin(None) == 1  # the legacy default stream cannot be captured
+    assert L.cf_graph_end(None, C.byref(h)) == 1
+    assert L.cf_graph_launch(None, None) == 1
+    assert L.cf_graph_nodes(None) == -1
+    assert L.cf_graph_destroy(None) == 0
+    r = B.cf_probe_result()
+    n = C.c_size_t(0)
+    assert L.cf_probe_ws_size(7, C.byref(n)) == 1
+    assert L.cf_probe(0, None, 0, 1, None, C.byref(r)) == 1

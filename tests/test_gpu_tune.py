@@ -1,0 +1,92 @@
+"""Every kernel configuration (cf_params.tune) against the FP64 oracle, and
+the autotuner (cf_autotune) with its cache file."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from _helpers import ATOL_S, TIE_EPS, greedy_margin, valid_matching  # noqa: E402
+from gen import config2  # noqa: E402
+from paper_1707_02423_gb300 import _binding as B  # noqa: E402
+from paper_1707_02423_gb300 import api  # noqa: E402
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def wl():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1707_02423_gb300 import build
+
+    build.build()
+    # 22 CFGs, n in [8, 120]: warp-, quarter-, CTA- and global-class pairs
+    w = config2(22)
+    om = np.linspace(0.6, 1.4, w.F)
+    ref = []
+    for a, b in w.pairs:
+        X = oracle.similarity(w.cfgs_a[a], w.cfgs_a[b], om, 0.8, 40)["X"]
+        m, s = oracle.greedy_match(X)
+        ref.append((greedy_margin(X) > TIE_EPS, m, s, X))
+    pa = api.Pack(w.cfgs_a, w.F, device=DEV)
+    return w, pa, torch.tensor(om, dtype=torch.float32, device=DEV), ref
+
+
+NT = 72
+
+
+def test_tune_table():
+    L = B.lib()
+    assert L.cf_num_tunes() == NT
+    seen = set()
+    for t in range(0, NT + 1):
+        d = api.tune_info(t)
+        assert d["threads_per_cta"] in (512, 1024)
+        assert d["smallest_group"] in (32, d["threads_per_cta"] // 4, d["threads_per_cta"])
+        assert d["cluster"] in (0, 2, 4, 8)
+        if t > 0:
+            seen.add((d["threads_per_cta"], d["smallest_group"], d["matching"], d["cluster"]))
+    assert len(seen) == NT
+    assert api.tune_info(0) == {**api.tune_info(1), "tune": 0}
+
+
+@pytest.mark.parametrize("tune", list(range(1, NT + 1, 5)) + [18, 19, 36, 37, 54, 55, 72])
+def test_every_tune_matches_oracle(wl, tune):
+    w, pa, om, ref = wl
+    res = api.similarity(pa, pa, w.pairs, om, 0.8, 40, want_match=True, tune=tune)
+    scores = res.scores.cpu().numpy()
+    match = res.match.cpu().numpy()
+    for p, (a, b) in enumerate(w.pairs):
+        clear, m_ref, s_ref, X = ref[p]
+        m = match[res.m_off[p]:res.m_off[p + 1]]
+        assert valid_matching(m, w.cfgs_a[a].n, w.cfgs_a[b].n), p
+        if clear:
+            assert np.array_equal(m, m_ref), (tune, p)
+            assert abs(float(scores[p]) - s_ref) <= ATOL_S, (tune, p)
+        else:
+            s_own = sum(X[i, m[i]] for i in range(len(m)) if m[i] >= 0)
+            assert abs(float(scores[p]) - s_own) <= ATOL_S, (tune, p)
+
+
+def test_autotune_picks_a_tune_and_caches_it(wl, tmp_path):
+    w, pa, om, ref = wl
+    cache = str(tmp_path / "tune.cache")
+    t1, ms1 = api.autotune(pa, pa, w.pairs, om, cache_path=cache)
+    assert 1 <= t1 <= NT and ms1 > 0.0
+    lines = open(cache).read().split("\n")
+    assert len([x for x in lines if x.strip()]) == 1
+    key, tid, ms = lines[0].split()
+    assert int(tid) == t1 and "sm=" in key and "K=40" in key
+    t2, ms2 = api.autotune(pa, pa, w.pairs, om, cache_path=cache)  # cache hit: no timing
+    assert (t2, round(ms2, 4)) == (t1, round(ms1, 4))
+    assert len([x for x in open(cache).read().split("\n") if x.strip()]) == 1
+    # a different K is a different key
+    t3, _ = api.autotune(pa, pa, w.pairs, om, K=20, cache_path=cache)
+    assert 1 <= t3 <= NT
+    assert len([x for x in open(cache).read().split("\n") if x.strip()]) == 2
+    # the picked tune computes the same scores as the default within the bar
+    r0 = api.similarity(pa, pa, w.pairs, om, want_match=True)
+    r1 = api.similarity(pa, pa, w.pairs, om, want_match=True, tune=t1)
+    assert float((r0.scores - r1.scores).abs().max()) <= 2 * ATOL_S
