@@ -20,12 +20,16 @@
 // segments backwards, recomputing each segment's iterates from its checkpoint
 // (about 2K forward steps and K adjoint steps; S + K/S + 1 matrices resident).
 //
-// One 256-thread CTA per pair, all matrices in a scratch slot of the
-// workspace (L2-resident).  Element loops run a warp per row and the lanes
-// over columns.  An edge's gradient is a warp-reduced sum owned by one warp
-// per step, accumulated in the slot and added to a per-pack distinct-edge
-// array when the pair is done; a last kernel adds those to the caller's
-// user-order buffers.
+// A pair runs on a team: one 256-thread CTA, or -- for the pairs too large
+// for one CTA's shared memory in the forward, whose single-CTA adjoint would
+// be the critical path of a batch -- all CTAs of a thread-block cluster.  All
+// matrices live in a scratch slot of the workspace (L2-resident).  Element
+// loops run a team warp per row and the lanes over columns.  An edge's
+// gradient is a warp-reduced sum owned by one team warp per step,
+// accumulated in the slot and added to a per-pack distinct-edge array when
+// the pair is done; a last kernel adds those to the caller's user-order
+// buffers.  Team syncs are CTA barriers or cluster barriers (release /
+// acquire at cluster scope, which orders the slot's global-memory traffic).
 #include "device_common.cuh"
 #include "kernels.h"
 
@@ -36,13 +40,32 @@ namespace {
 constexpr int kBwdNT = 256;
 constexpr int kBwdWarps = kBwdNT / 32;
 
-__device__ __forceinline__ float block_sum(float v, float* red, int par) {
-  v = warp_sum(v);
-  const int lane = threadIdx.x & 31;
-  if (lane == 0) red[par * 32 + (threadIdx.x >> 5)] = v;
-  __syncthreads();
-  return warp_sum(lane < kBwdWarps ? red[par * 32 + lane] : 0.f);
-}
+// The threads working on one pair: one CTA (C == 1) or the C CTAs of a
+// cluster.  Ranks and warps are numbered across the team.
+struct Team {
+  int rank, size, warp, nwarps, C;
+  float* red;             // this CTA's per-warp partials, two parities
+  float* part;            // this CTA's partial sums, two parities (cluster teams)
+  const uint32_t* paddr;  // cluster address of every CTA's part[] (cluster teams)
+  __device__ __forceinline__ void sync() const {
+    if (C == 1)
+      __syncthreads();
+    else
+      cl_sync();
+  }
+  // Sum over the team, the same bits on every thread.
+  __device__ __forceinline__ float sum(float v, int par) const {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) red[par * 32 + w] = v;
+    __syncthreads();
+    const float cta = warp_sum(lane < kBwdWarps ? red[par * 32 + lane] : 0.f);
+    if (C == 1) return cta;
+    if (threadIdx.x == 0) part[par] = cta;
+    cl_sync();
+    return warp_sum(lane < C ? cl_ld_f32(paddr[lane] + 4u * par) : 0.f);
+  }
+};
 
 struct BwdPair {
   int p, na, nb, ea, eb;
@@ -69,6 +92,7 @@ struct BwdCtx {
   float alpha;
   int K, norm_mode, F, Fp;
   uint32_t n_pairs;  // valid pairs in the queue
+  uint32_t n_big;    // the leading pairs that take a cluster when clusters are launched
 };
 
 // Successor-pair plus predecessor-pair sum of Y at entry (i, j), both graphs'
@@ -102,30 +126,31 @@ __device__ __forceinline__ float gather_mem(const float* Y, const BwdPair& q, in
 
 // One forward step from X (normalised) into Xn:  Y = alpha/2 M(X) + (1-alpha) Ehat,
 // Xn = Y / |Y| (or Y).  Returns |Y| (1 when not renormalised).
-__device__ __forceinline__ float fwd_step(const BwdCtx& cx, const BwdPair& q, const float* X, float* Xn, const float* eh, float* red,
-                          int& par) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+__device__ __forceinline__ float fwd_step(const BwdCtx& cx, const BwdPair& q, const float* X, float* Xn, const float* eh,
+                                          const Team& tm, int& par) {
+  const int lane = threadIdx.x & 31;
   const float ca = 0.5f * cx.alpha, cb = 1.f - cx.alpha;
   float ss = 0.f;
-  for (int i = w; i < q.na; i += kBwdWarps)
+  for (int i = tm.warp; i < q.na; i += tm.nwarps)
     for (int j = lane; j < q.nb; j += 32) {
       const size_t o = (size_t)i * q.nb + j;
       const float y = fmaf(ca, gather_mem(X, q, i, j), cb * eh[o]);
       Xn[o] = y;
       ss = fmaf(y, y, ss);
     }
-  const float yy = block_sum(ss, red, par);
+  const float yy = tm.sum(ss, par);
   par ^= 1;
   if (cx.norm_mode != 0) return 1.f;
   const float nY = sqrtf(yy), inv = 1.f / nY;
-  for (int i = w; i < q.na; i += kBwdWarps)
+  for (int i = tm.warp; i < q.na; i += tm.nwarps)
     for (int j = lane; j < q.nb; j += 32) Xn[(size_t)i * q.nb + j] *= inv;
-  __syncthreads();
+  tm.sync();
   return nY;
 }
 
-__device__ __forceinline__ void run_pair_bwd(const BwdCtx& cx, const BwdPair& q, float* slot, float* red) {
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+__device__ __forceinline__ void run_pair_bwd(const BwdCtx& cx, const BwdPair& q, float* slot, const Team& tm) {
+  const int t = tm.rank, lane = threadIdx.x & 31, w = tm.warp;
+  const int TN = tm.size, TW = tm.nwarps;
   const int na = q.na, nb = q.nb;
   const size_t E = (size_t)na * nb;
   const int K = cx.K, S = bwd_segment(K), nck = K / S + 1;
@@ -154,7 +179,7 @@ __device__ __forceinline__ void run_pair_bwd(const BwdCtx& cx, const BwdPair& q,
   int par = 0;
 
   // both graphs' edge lists (CFG-local distinct-edge order), zeroed accumulators
-  for (int i = t; i < na; i += kBwdNT)
+  for (int i = t; i < na; i += TN)
     for (int e = __ldg(q.ao + i), e1 = __ldg(q.ao + i + 1); e < e1; ++e) {
       const CfAdj a = ldg_adj(q.aoa + e);
       const int l = e - q.a_edge0;
@@ -163,7 +188,7 @@ __device__ __forceinline__ void run_pair_bwd(const BwdCtx& cx, const BwdPair& q,
       aw[l] = a.w;
       ga[l] = 0.f;
     }
-  for (int j = t; j < nb; j += kBwdNT)
+  for (int j = t; j < nb; j += TN)
     for (int e = __ldg(q.bo + j), e1 = __ldg(q.bo + j + 1); e < e1; ++e) {
       const CfAdj b = ldg_adj(q.boa + e);
       const int l = e - q.b_edge0;
@@ -173,11 +198,11 @@ __device__ __forceinline__ void run_pair_bwd(const BwdCtx& cx, const BwdPair& q,
       gb[l] = 0.f;
     }
   // E, |E|, Ehat = X_0 (checkpoint 0)
-  for (int i = t; i < na; i += kBwdNT) rn[i] = attr_norm(q.aat + (size_t)i * cx.Fp, cx.om, cx.Fp);
-  for (int j = t; j < nb; j += kBwdNT) cn[j] = attr_norm(q.bat + (size_t)j * cx.Fp, cx.om, cx.Fp);
-  __syncthreads();
+  for (int i = t; i < na; i += TN) rn[i] = attr_norm(q.aat + (size_t)i * cx.Fp, cx.om, cx.Fp);
+  for (int j = t; j < nb; j += TN) cn[j] = attr_norm(q.bat + (size_t)j * cx.Fp, cx.om, cx.Fp);
+  tm.sync();
   float ss = 0.f;
-  for (int i = w; i < na; i += kBwdWarps)
+  for (int i = w; i < na; i += TW)
     for (int j = lane; j < nb; j += 32) {
       const float dot = attr_dot(q.aat + (size_t)i * cx.Fp, q.bat + (size_t)j * cx.Fp, cx.om, cx.Fp);
       const float den = rn[i] * cn[j];
@@ -185,11 +210,11 @@ __device__ __forceinline__ void run_pair_bwd(const BwdCtx& cx, const BwdPair& q,
       er[(size_t)i * nb + j] = e;
       ss = fmaf(e, e, ss);
     }
-  const float nE = sqrtf(block_sum(ss, red, par));
+  const float nE = sqrtf(tm.sum(ss, par));
   par ^= 1;
   const float inv = nE > 0.f ? 1.f / nE : 0.f;
   const float uni = 1.f / sqrtf((float)na * (float)nb);
-  for (int i = w; i < na; i += kBwdWarps)
+  for (int i = w; i < na; i += TW)
     for (int j = lane; j < nb; j += 32) {
       const size_t o = (size_t)i * nb + j;
       const float v = nE > 0.f ? er[o] * inv : uni;
@@ -197,63 +222,63 @@ __device__ __forceinline__ void run_pair_bwd(const BwdCtx& cx, const BwdPair& q,
       ck[o] = v;
     }
   if (t == 0) nrm[0] = 1.f;
-  __syncthreads();
+  tm.sync();
 
   // forward, keeping X every S steps
   const float* X = ck;
   for (int k = 0; k < K; ++k) {
     float* dst = ((k + 1) % S == 0) ? ck + (size_t)((k + 1) / S) * E : sg + (size_t)((k + 1) % S) * E;
-    const float nY = fwd_step(cx, q, X, dst, eh, red, par);
+    const float nY = fwd_step(cx, q, X, dst, eh, tm, par);
     if (t == 0) nrm[k + 1] = nY;
     X = dst;
   }
   // Xbar_K = g 1[matched], Ehatbar = 0
-  for (int i = w; i < na; i += kBwdWarps)
+  for (int i = w; i < na; i += TW)
     for (int j = lane; j < nb; j += 32) {
       const size_t o = (size_t)i * nb + j;
       xb[o] = 0.f;
       ehb[o] = 0.f;
     }
-  __syncthreads();
+  tm.sync();
   const float g = cx.gbar[q.p];
-  for (int i = t; i < na; i += kBwdNT) {
+  for (int i = t; i < na; i += TN) {
     const int m = cx.match[cx.m_off[q.p] + i];
     if (m >= 0 && m < nb) xb[(size_t)i * nb + m] = g;
   }
-  __syncthreads();
+  tm.sync();
 
   // adjoint sweep, one segment at a time from the last
   for (int seg = (K - 1) / S; seg >= 0 && K > 0; --seg) {
     const int k0 = seg * S, k1 = min(K, k0 + S);
-    for (int i = w; i < na; i += kBwdWarps)
+    for (int i = w; i < na; i += TW)
       for (int j = lane; j < nb; j += 32) sg[(size_t)i * nb + j] = ck[(size_t)seg * E + (size_t)i * nb + j];
-    __syncthreads();
-    for (int k = k0; k < k1 - 1; ++k) fwd_step(cx, q, sg + (size_t)(k - k0) * E, sg + (size_t)(k - k0 + 1) * E, eh, red, par);
+    tm.sync();
+    for (int k = k0; k < k1 - 1; ++k) fwd_step(cx, q, sg + (size_t)(k - k0) * E, sg + (size_t)(k - k0 + 1) * E, eh, tm, par);
     // the segment's last iterate X_{k1} is the next checkpoint (or X_K)
     const float* Xend = (k1 % S == 0) ? ck + (size_t)(k1 / S) * E : sg + (size_t)(k1 - k0) * E;
-    if (k1 % S != 0) fwd_step(cx, q, sg + (size_t)(k1 - 1 - k0) * E, sg + (size_t)(k1 - k0) * E, eh, red, par);
+    if (k1 % S != 0) fwd_step(cx, q, sg + (size_t)(k1 - 1 - k0) * E, sg + (size_t)(k1 - k0) * E, eh, tm, par);
     for (int k = k1 - 1; k >= k0; --k) {
       const float* X1 = (k + 1 == k1) ? Xend : sg + (size_t)(k + 1 - k0) * E;
       const float* Xk = sg + (size_t)(k - k0) * E;
       float d = 0.f;
       if (cx.norm_mode == 0) {
         float acc = 0.f;
-        for (int i = w; i < na; i += kBwdWarps)
+        for (int i = w; i < na; i += TW)
           for (int j = lane; j < nb; j += 32) acc = fmaf(xb[(size_t)i * nb + j], X1[(size_t)i * nb + j], acc);
-        d = block_sum(acc, red, par);
+        d = tm.sum(acc, par);
         par ^= 1;
       }
       const float invY = cx.norm_mode == 0 ? 1.f / nrm[k + 1] : 1.f;
-      for (int i = w; i < na; i += kBwdWarps)
+      for (int i = w; i < na; i += TW)
         for (int j = lane; j < nb; j += 32) {
           const size_t o = (size_t)i * nb + j;
           const float yb = (xb[o] - d * X1[o]) * invY;
           ehb[o] = fmaf(1.f - cx.alpha, yb, ehb[o]);
           zb[o] = cx.alpha * yb;
         }
-      __syncthreads();
+      tm.sync();
       // edge gradients at this step
-      for (int e = w; e < q.ea; e += kBwdWarps) {
+      for (int e = w; e < q.ea; e += TW) {
         const int p = asrc[e], qq = adst[e];
         float s = 0.f;
         for (int f = lane; f < q.eb; f += 32) {
@@ -264,7 +289,7 @@ __device__ __forceinline__ void run_pair_bwd(const BwdCtx& cx, const BwdPair& q,
         s = warp_sum(s);
         if (lane == 0) ga[e] = fmaf(0.5f, s, ga[e]);
       }
-      for (int f = w; f < q.eb; f += kBwdWarps) {
+      for (int f = w; f < q.eb; f += TW) {
         const int j = bsrc[f], v = bdst[f];
         float s = 0.f;
         for (int e = lane; e < q.ea; e += 32) {
@@ -276,30 +301,30 @@ __device__ __forceinline__ void run_pair_bwd(const BwdCtx& cx, const BwdPair& q,
         if (lane == 0) gb[f] = fmaf(0.5f, s, gb[f]);
       }
       // Xbar_k = 1/2 M(Zbar)
-      for (int i = w; i < na; i += kBwdWarps)
+      for (int i = w; i < na; i += TW)
         for (int j = lane; j < nb; j += 32) xb[(size_t)i * nb + j] = 0.5f * gather_mem(zb, q, i, j);
-      __syncthreads();
+      tm.sync();
     }
   }
   // Ehatbar += Xbar_0
-  for (int i = w; i < na; i += kBwdWarps)
+  for (int i = w; i < na; i += TW)
     for (int j = lane; j < nb; j += 32) ehb[(size_t)i * nb + j] += xb[(size_t)i * nb + j];
-  __syncthreads();
+  tm.sync();
 
   // omega gradient through the cosine term (rows / columns with a zero norm have E = 0 and no gradient)
   if (cx.gomega && nE > 0.f) {
     float acc = 0.f;
-    for (int i = w; i < na; i += kBwdWarps)
+    for (int i = w; i < na; i += TW)
       for (int j = lane; j < nb; j += 32) acc = fmaf(ehb[(size_t)i * nb + j], eh[(size_t)i * nb + j], acc);
-    const float d = block_sum(acc, red, par);
+    const float d = tm.sum(acc, par);
     par ^= 1;
-    for (int i = w; i < na; i += kBwdWarps)
+    for (int i = w; i < na; i += TW)
       for (int j = lane; j < nb; j += 32) {
         const size_t o = (size_t)i * nb + j;
         ehb[o] = (ehb[o] - d * eh[o]) / nE;  // Ebar
       }
-    __syncthreads();
-    for (int i = w; i < na; i += kBwdWarps) {
+    tm.sync();
+    for (int i = w; i < na; i += TW) {
       float r = 0.f;
       for (int j = lane; j < nb; j += 32) r = fmaf(ehb[(size_t)i * nb + j], er[(size_t)i * nb + j], r);
       r = warp_sum(r);
@@ -312,14 +337,14 @@ __device__ __forceinline__ void run_pair_bwd(const BwdCtx& cx, const BwdPair& q,
         if (lane == 0) Rf[(size_t)i * cx.Fp + f] = s;
       }
     }
-    for (int j = w; j < nb; j += kBwdWarps) {
+    for (int j = w; j < nb; j += TW) {
       float s = 0.f;
       for (int i = lane; i < na; i += 32) s = fmaf(ehb[(size_t)i * nb + j], er[(size_t)i * nb + j], s);
       s = warp_sum(s);
       if (lane == 0) gam[j] = s;
     }
-    __syncthreads();
-    for (int f = t; f < cx.F; f += kBwdNT) {
+    tm.sync();
+    for (int f = t; f < cx.F; f += TN) {
       float g1 = 0.f, g2 = 0.f, g3 = 0.f;
       for (int i = 0; i < na; ++i)
         if (rn[i] > 0.f) {
@@ -336,18 +361,15 @@ __device__ __forceinline__ void run_pair_bwd(const BwdCtx& cx, const BwdPair& q,
     }
   }
   // this pair's edge gradients into the packs' distinct-edge accumulators
-  for (int e = t; e < q.ea; e += kBwdNT) atomicAdd(cx.gcan_a + q.a_edge0 + e, ga[e]);
-  for (int f = t; f < q.eb; f += kBwdNT) atomicAdd(cx.gcan_b + q.b_edge0 + f, gb[f]);
-  __syncthreads();
+  for (int e = t; e < q.ea; e += TN) atomicAdd(cx.gcan_a + q.a_edge0 + e, ga[e]);
+  for (int f = t; f < q.eb; f += TN) atomicAdd(cx.gcan_b + q.b_edge0 + f, gb[f]);
+  tm.sync();
 }
 
-__global__ void __launch_bounds__(kBwdNT, 1) bwd_kernel(CallArgs a) {
-  __shared__ __align__(16) float s_om[kMaxF];
-  __shared__ float s_red[64];
-  __shared__ BwdCtx s_cx;
-  __shared__ uint32_t s_q;
+// Per-CTA setup by thread 0 into shared memory: pack views, workspace
+// pointers, omega.
+__device__ __forceinline__ void bwd_setup(const CallArgs& a, BwdCtx& c, float* s_om) {
   if (threadIdx.x == 0) {
-    BwdCtx& c = s_cx;
     c.A = load_pack(a.pack_a);
     c.B = load_pack(a.pack_b);
     const WsLayout L = ws_layout(a.P);
@@ -374,11 +396,47 @@ __global__ void __launch_bounds__(kBwdNT, 1) bwd_kernel(CallArgs a) {
     uint32_t n = 0;
     for (int k = 0; k < kNumClasses; ++k) n += c.hdr->n_class[k];
     c.n_pairs = n;
+    // the pairs that fit no single CTA's shared memory in the forward lead the queue
+    c.n_big = c.hdr->n_class[kClassGlobal] + c.hdr->n_class[kClassCluster];
   }
   __syncthreads();
-  const BwdCtx& cx = s_cx;
-  if (threadIdx.x < kMaxF) s_om[threadIdx.x] = threadIdx.x < cx.F ? a.omega[threadIdx.x] : 0.f;
+  if (threadIdx.x < kMaxF) s_om[threadIdx.x] = threadIdx.x < c.F ? a.omega[threadIdx.x] : 0.f;
   __syncthreads();
+}
+
+__device__ __forceinline__ BwdPair bwd_pair(const BwdCtx& cx, uint32_t qi) {
+  BwdPair q;
+  q.p = (int)cx.queue[qi];
+  const int pa = cx.pairs[2 * q.p], pb = cx.pairs[2 * q.p + 1];
+  const int ba = cx.A.node_off[pa], bb = cx.B.node_off[pb];
+  q.na = cx.A.node_off[pa + 1] - ba;
+  q.nb = cx.B.node_off[pb + 1] - bb;
+  q.a_edge0 = cx.A.edge_off[pa];
+  q.b_edge0 = cx.B.edge_off[pb];
+  q.ea = cx.A.edge_off[pa + 1] - q.a_edge0;
+  q.eb = cx.B.edge_off[pb + 1] - q.b_edge0;
+  q.ao = cx.A.out_ptr + ba;
+  q.ai = cx.A.in_ptr + ba;
+  q.bo = cx.B.out_ptr + bb;
+  q.bi = cx.B.in_ptr + bb;
+  q.aoa = cx.A.out_adj;
+  q.aia = cx.A.in_adj;
+  q.boa = cx.B.out_adj;
+  q.bia = cx.B.in_adj;
+  q.aat = cx.A.attr + (size_t)ba * cx.Fp;
+  q.bat = cx.B.attr + (size_t)bb * cx.Fp;
+  return q;
+}
+
+// One CTA per pair.  first: where in the queue this kernel starts (after the
+// pairs a cluster launch took, or 0).
+__global__ void __launch_bounds__(kBwdNT, 1) bwd_kernel(CallArgs a, uint32_t first) {
+  __shared__ __align__(16) float s_om[kMaxF];
+  __shared__ float s_red[64];
+  __shared__ BwdCtx s_cx;
+  __shared__ uint32_t s_q;
+  bwd_setup(a, s_cx, s_om);
+  const BwdCtx& cx = s_cx;
   const uint64_t need = cx.hdr->bwd_slot_need;
   const uint64_t nslots = need ? cx.slots_bytes / need : 0;
   if (nslots == 0) {
@@ -387,33 +445,53 @@ __global__ void __launch_bounds__(kBwdNT, 1) bwd_kernel(CallArgs a) {
   }
   if (blockIdx.x >= nslots) return;
   float* slot = reinterpret_cast<float*>(cx.slots + (size_t)blockIdx.x * need);
+  const Team tm{(int)threadIdx.x, kBwdNT, (int)threadIdx.x >> 5, kBwdWarps, 1, s_red, nullptr, nullptr};
+  const uint32_t start = first == 0xffffffffu ? cx.n_big : (first > cx.n_pairs ? cx.n_pairs : first);
   for (;;) {
-    if (threadIdx.x == 0) s_q = atomicAdd(&cx.hdr->q_bwd, 1u);
+    if (threadIdx.x == 0) s_q = start + atomicAdd(&cx.hdr->q_bwd, 1u);
     __syncthreads();
     const uint32_t qi = s_q;
     __syncthreads();
     if (qi >= cx.n_pairs) break;
-    BwdPair q;
-    q.p = (int)cx.queue[qi];
-    const int pa = cx.pairs[2 * q.p], pb = cx.pairs[2 * q.p + 1];
-    const int ba = cx.A.node_off[pa], bb = cx.B.node_off[pb];
-    q.na = cx.A.node_off[pa + 1] - ba;
-    q.nb = cx.B.node_off[pb + 1] - bb;
-    q.a_edge0 = cx.A.edge_off[pa];
-    q.b_edge0 = cx.B.edge_off[pb];
-    q.ea = cx.A.edge_off[pa + 1] - q.a_edge0;
-    q.eb = cx.B.edge_off[pb + 1] - q.b_edge0;
-    q.ao = cx.A.out_ptr + ba;
-    q.ai = cx.A.in_ptr + ba;
-    q.bo = cx.B.out_ptr + bb;
-    q.bi = cx.B.in_ptr + bb;
-    q.aoa = cx.A.out_adj;
-    q.aia = cx.A.in_adj;
-    q.boa = cx.B.out_adj;
-    q.bia = cx.B.in_adj;
-    q.aat = cx.A.attr + (size_t)ba * cx.Fp;
-    q.bat = cx.B.attr + (size_t)bb * cx.Fp;
-    run_pair_bwd(cx, q, slot, s_red);
+    run_pair_bwd(cx, bwd_pair(cx, qi), slot, tm);
+  }
+}
+
+// The large pairs (queue[0, n_big)) on clusters of C CTAs: CTA 0 pulls a pair
+// and every CTA reads its index through distributed shared memory; cluster
+// c uses scratch slot c.
+__global__ void __launch_bounds__(kBwdNT, 1) bwd_cluster_kernel(CallArgs a) {
+  __shared__ __align__(16) float s_om[kMaxF];
+  __shared__ float s_red[64];
+  __shared__ float s_part[2];
+  __shared__ uint32_t s_paddr[kMaxCluster];
+  __shared__ BwdCtx s_cx;
+  __shared__ uint32_t s_q, s_qaddr;
+  bwd_setup(a, s_cx, s_om);
+  const BwdCtx& cx = s_cx;
+  const int C = (int)cl_size(), rank = (int)cl_rank();
+  const uint32_t cid = cl_index();
+  if (cx.n_big == 0) return;  // the same on every CTA
+  const uint64_t need = cx.hdr->bwd_slot_need;
+  const uint64_t nslots = need ? cx.slots_bytes / need : 0;
+  if (nslots == 0) {
+    if (cid == 0 && rank == 0 && threadIdx.x == 0) set_status(cx.hdr, 2 /* CF_ERR_WORKSPACE */, -1);
+    return;
+  }
+  if (cid >= nslots) return;  // the whole cluster
+  if ((int)threadIdx.x < C) s_paddr[threadIdx.x] = cl_map(s_part, threadIdx.x);
+  if (threadIdx.x == 0) s_qaddr = cl_map(&s_q, 0);
+  __syncthreads();
+  float* slot = reinterpret_cast<float*>(cx.slots + (size_t)cid * need);
+  const Team tm{rank * kBwdNT + (int)threadIdx.x, C * kBwdNT, rank * kBwdWarps + ((int)threadIdx.x >> 5), C * kBwdWarps,
+                C, s_red, s_part, s_paddr};
+  for (;;) {
+    if (rank == 0 && threadIdx.x == 0) s_q = atomicAdd(&cx.hdr->q_bwd_big, 1u);
+    cl_sync();
+    const uint32_t qi = cl_ld_u32(s_qaddr);
+    cl_sync();  // CTA 0 overwrites s_q only after every CTA has read it
+    if (qi >= cx.n_big) break;
+    run_pair_bwd(cx, bwd_pair(cx, qi), slot, tm);
   }
 }
 
@@ -445,6 +523,24 @@ __global__ void bwd_scatter_kernel(CallArgs a, int side) {
 }
 
 int g_bwd_sm = 0;
+int g_bwd_clusters = -1;  // resident clusters of kBwdCluster CTAs, 0 if none fit
+
+constexpr int kBwdCluster = 8;
+
+cudaLaunchConfig_t bwd_cluster_cfg(int n_clusters, cudaLaunchAttribute* attr, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kBwdCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(n_clusters * kBwdCluster, 1, 1);
+  cfg.blockDim = dim3(kBwdNT, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
 
 }  // namespace
 
@@ -456,9 +552,25 @@ cudaError_t launch_backward(const CallArgs& a, cudaStream_t s) {
     e = cudaDeviceGetAttribute(&g_bwd_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
   }
+  if (g_bwd_clusters < 0) {
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = bwd_cluster_cfg(1, attr, s);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, bwd_cluster_kernel, &cfg) != cudaSuccess) n = 0;
+    cudaGetLastError();
+    g_bwd_clusters = n;
+  }
   bwd_zero_kernel<<<2 * g_bwd_sm, 256, 0, s>>>(a);
+  uint32_t first = 0;
+  if (g_bwd_clusters > 0) {  // the large pairs first, each on a cluster
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = bwd_cluster_cfg(g_bwd_clusters, attr, s);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, bwd_cluster_kernel, a);
+    if (e != cudaSuccess) return e;
+    first = 0xffffffffu;  // the CTA kernel starts after them (n_big, read on the device)
+  }
   const int grid = a.P < 2 * g_bwd_sm ? a.P : 2 * g_bwd_sm;
-  bwd_kernel<<<grid, kBwdNT, 0, s>>>(a);
+  bwd_kernel<<<grid, kBwdNT, 0, s>>>(a, first);
   if (a.grad_w_a) bwd_scatter_kernel<<<2 * g_bwd_sm, 256, 0, s>>>(a, 0);
   if (a.grad_w_b && a.pack_a != a.pack_b) bwd_scatter_kernel<<<2 * g_bwd_sm, 256, 0, s>>>(a, 1);
   return cudaGetLastError();

@@ -200,15 +200,16 @@ __device__ __forceinline__ float lds_at(ClusterY y, int a, int b) {
 // + (all of i) x (further ones of j)         col_extra: only lanes whose column has them
 // which covers every pair exactly once.  A = row i's first two out-neighbours
 // {u ld 4, w} (the sign bit of A.w flags further neighbours of i), Q = its
-// first two in-neighbours; padding entries carry weight 0.
+// first two in-neighbours; padding entries carry weight 0.  (The cluster
+// tier flags rows with a neighbour in another CTA by the sign bit of A.y.)
 template <class YT>
 __device__ __forceinline__ float gather_fast(YT Y, const int4 A, const int4 Q, const ColPad& c) {
   const float a0 = lds_at(Y, A.x, c.vo0), a1 = lds_at(Y, A.x, c.vo1);
   const float a2 = lds_at(Y, A.z, c.vo0), a3 = lds_at(Y, A.z, c.vo1);
   const float b0 = lds_at(Y, Q.x, c.vi0), b1 = lds_at(Y, Q.x, c.vi1);
   const float b2 = lds_at(Y, Q.z, c.vi0), b3 = lds_at(Y, Q.z, c.vi1);
-  const float so =
-      fmaf(fabsf(__int_as_float(A.w)), fmaf(c.wo1, a3, c.wo0 * a2), __int_as_float(A.y) * fmaf(c.wo1, a1, c.wo0 * a0));
+  const float so = fmaf(fabsf(__int_as_float(A.w)), fmaf(c.wo1, a3, c.wo0 * a2),
+                        fabsf(__int_as_float(A.y)) * fmaf(c.wo1, a1, c.wo0 * a0));
   const float si =
       fmaf(__int_as_float(Q.w), fmaf(c.wi1, b3, c.wi0 * b2), __int_as_float(Q.y) * fmaf(c.wi1, b1, c.wi0 * b0));
   return so + si;
@@ -236,7 +237,7 @@ __device__ __forceinline__ float col_extra(YT Y, const int4 A, const int4 Q, con
   float s = 0.f;
   for (int f = c.xo0; f < c.xo1; ++f) {
     const int2 v = cedge[f];
-    float t = fmaf(fabsf(__int_as_float(A.w)), lds_at(Y, A.z, v.x), __int_as_float(A.y) * lds_at(Y, A.x, v.x));
+    float t = fmaf(fabsf(__int_as_float(A.w)), lds_at(Y, A.z, v.x), fabsf(__int_as_float(A.y)) * lds_at(Y, A.x, v.x));
     for (int k = rr.x + 2; k < rr.y; ++k) {
       const int2 e = redge[k];
       t = fmaf(__int_as_float(e.y), lds_at(Y, e.x, v.x), t);
@@ -305,8 +306,8 @@ __device__ __forceinline__ float gather_g(const float* Y, int ld, const Geo& g, 
 // is locally dominant), so the loop is bounded by min(n_row, n_col) rounds; if
 // the bound is reached first (NaN in X) the status word gets CF_ERR_NUMERIC.
 // Returns the score on every thread; writes match[n_a] if given.
-template <class IdxT>
-__device__ __forceinline__ float greedy(const Group& grp, const float* X, int ld, int n_row, int n_col, int tr,
+template <class IdxT, class Grp>
+__device__ __forceinline__ float greedy(const Grp& grp, const float* X, int ld, int n_row, int n_col, int tr,
                                         IdxT* rb, IdxT* cb, int32_t* mo, WsHeader* hdr, int pidx) {
   const int t = grp.rank, G = grp.size, lane = t & 31, w = grp.warp(), NW = grp.nwarps();
   for (int r = t; r < n_row; r += G) rb[r] = (IdxT)-2;
@@ -931,51 +932,16 @@ __global__ void __launch_bounds__(NT, 1) fwd_batched_kernel(CallArgs a, int per_
 // writes of Y_{k+2} into the same buffer.  X_K is then written to the
 // cluster's scratch slot and CTA 0 runs the greedy matching on it.
 
-__device__ __forceinline__ uint32_t cl_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cl_size() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cl_index() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
-  return r;
-}
-// shared::cluster address of the same shared-memory location in CTA `rank`
-__device__ __forceinline__ uint32_t cl_map(const void* p, uint32_t rank) {
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
-  return r;
-}
-// All threads of all CTAs of the cluster; release / acquire at cluster scope.
-// The CTAs of a cluster are co-scheduled, so every arrival happens.
-__device__ __forceinline__ void cl_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__device__ __forceinline__ float cl_ld_f32(uint32_t addr) {
-  float v;
-  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
-  return v;
-}
-__device__ __forceinline__ uint32_t cl_ld_u32(uint32_t addr) {
-  uint32_t v;
-  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
-  return v;
-}
-
 // Shared state of the cluster kernel besides the pair region.
 struct ClState {
   float part[2];       // this CTA's partial sum, two parities
   float redw[64];      // per-warp partials, two parities
+  int parti[2];        // the same for integer sums
+  int redwi[64];
   uint32_t q;          // the pair index CTA 0 pulled
   uint32_t rbase[kMaxCluster];  // cluster address of each CTA's region
   uint32_t paddr[kMaxCluster];  // cluster address of each CTA's part[]
+  uint32_t piaddr[kMaxCluster]; // cluster address of each CTA's parti[]
   uint32_t qaddr;               // cluster address of CTA 0's q
 };
 
@@ -995,6 +961,32 @@ __device__ __forceinline__ float cl_sum(float v, int par, ClState& st, int C) {
   return warp_sum(lane < C ? cl_ld_f32(st.paddr[lane] + 4u * par) : 0.f);
 }
 
+__device__ __forceinline__ int cl_sum_i(int v, int par, ClState& st, int C) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, NW = blockDim.x >> 5;
+  v = warp_sum_i(v);
+  if (lane == 0) st.redwi[par * 32 + w] = v;
+  __syncthreads();
+  if (w == 0) {
+    const int x = warp_sum_i(lane < NW ? st.redwi[par * 32 + lane] : 0);
+    if (lane == 0) st.parti[par] = x;
+  }
+  cl_sync();
+  return warp_sum_i(lane < C ? (int)cl_ld_u32(st.piaddr[lane] + 4u * par) : 0);
+}
+
+// Every thread of a cluster as one group (the interface of Group): ranks and
+// warps numbered across the CTAs, cluster barriers, cluster-wide sums.  The
+// greedy matching runs on it with its state in global memory.
+struct ClGroup {
+  int rank, size, C;
+  ClState* st;
+  __device__ __forceinline__ int warp() const { return rank >> 5; }
+  __device__ __forceinline__ int nwarps() const { return size >> 5; }
+  __device__ __forceinline__ void sync() const { cl_sync(); }
+  __device__ __forceinline__ float sum(float v, int par) const { return cl_sum(v, par, *st, C); }
+  __device__ __forceinline__ int sum_i(int v, int par) const { return cl_sum_i(v, par, *st, C); }
+};
+
 __device__ __noinline__ void run_pair_c(const Ctx& cx, const Geo& g, const Group& grp, int C, int rank, float* slot,
                                         unsigned char* region, ClState& st) {
   const Shape& s = g.s;
@@ -1011,8 +1003,12 @@ __device__ __noinline__ void run_pair_c(const Ctx& cx, const Geo& g, const Group
   int4* rq = ra + slab;
   int4* rr = rq + slab;
   int2* redge = reinterpret_cast<int2*>(rr + slab);
-  // cluster address of row u (of the whole row graph) in its owner's buffer 0
-  auto caddr = [&](int u) -> int {
+  // Row u (of the whole row graph) as the gathers address it: for a row whose
+  // neighbours all lie in this CTA's slab, the byte offset of u in this CTA's
+  // buffer (plain shared loads); otherwise the cluster address of u in its
+  // owner's buffer 0 (ld.shared::cluster), and A.y of the row is flagged.
+  auto raddr = [&](int u, bool remote) -> int {
+    if (!remote) return (u - i0) * ld * 4;
     const int o = u / slab;
     return (int)(st.rbase[o] + 4u * (uint32_t)nn + 4u * (uint32_t)((u - o * slab) * ld));
   };
@@ -1038,21 +1034,33 @@ __device__ __noinline__ void run_pair_c(const Ctx& cx, const Geo& g, const Group
     const int i = i0 + lr;
     const int o0 = __ldg(g.r_optr + i) - eo0, o1 = __ldg(g.r_optr + i + 1) - eo0;
     const int q0 = __ldg(g.r_iptr + i) - ei0, q1 = __ldg(g.r_iptr + i + 1) - ei0;
-    const CfAdj z{0, 0.f};
+    bool remote = false;
+    for (int e = o0; e < o1; ++e) {
+      const int u = __ldg(&g.r_oadj[eo0 + e].nbr);
+      remote |= u < i0 || u >= i0 + slab;
+    }
+    for (int e = q0; e < q1; ++e) {
+      const int u = __ldg(&g.r_iadj[ei0 + e].nbr);
+      remote |= u < i0 || u >= i0 + slab;
+    }
+    const CfAdj z{i0, 0.f};  // padding: a valid row of this CTA's slab, weight 0
     const CfAdj a0 = o1 > o0 ? ldg_adj(g.r_oadj + eo0 + o0) : z, a1 = o1 > o0 + 1 ? ldg_adj(g.r_oadj + eo0 + o0 + 1) : z;
     const CfAdj b0 = q1 > q0 ? ldg_adj(g.r_iadj + ei0 + q0) : z, b1 = q1 > q0 + 1 ? ldg_adj(g.r_iadj + ei0 + q0 + 1) : z;
     const int flag = (o1 - o0 > 2 || q1 - q0 > 2) ? (int)0x80000000 : 0;
-    ra[lr] = make_int4(caddr(a0.nbr), __float_as_int(a0.w), caddr(a1.nbr), __float_as_int(a1.w) | flag);
-    rq[lr] = make_int4(caddr(b0.nbr), __float_as_int(b0.w), caddr(b1.nbr), __float_as_int(b1.w));
+    const int rflag = remote ? (int)0x80000000 : 0;
+    ra[lr] = make_int4(raddr(a0.nbr, remote), __float_as_int(a0.w) | rflag, raddr(a1.nbr, remote),
+                       __float_as_int(a1.w) | flag);
+    rq[lr] = make_int4(raddr(b0.nbr, remote), __float_as_int(b0.w), raddr(b1.nbr, remote), __float_as_int(b1.w));
     rr[lr] = make_int4(o0 - so0, o1 - so0, n_so + q0 - si0, n_so + q1 - si0);
-  }
-  for (int k = t; k < n_so; k += G) {
-    const CfAdj a = ldg_adj(g.r_oadj + eo0 + so0 + k);
-    redge[k] = make_int2(caddr(a.nbr), __float_as_int(a.w));
-  }
-  for (int k = t; k < n_si; k += G) {
-    const CfAdj b = ldg_adj(g.r_iadj + ei0 + si0 + k);
-    redge[n_so + k] = make_int2(caddr(b.nbr), __float_as_int(b.w));
+    // this row's full lists, addressed the same way
+    for (int e = o0; e < o1; ++e) {
+      const CfAdj a = ldg_adj(g.r_oadj + eo0 + e);
+      redge[e - so0] = make_int2(raddr(a.nbr, remote), __float_as_int(a.w));
+    }
+    for (int e = q0; e < q1; ++e) {
+      const CfAdj b = ldg_adj(g.r_iadj + ei0 + e);
+      redge[n_so + e - si0] = make_int2(raddr(b.nbr, remote), __float_as_int(b.w));
+    }
   }
   for (int lr = t; lr < rows; lr += G) buf1[lr] = attr_norm(g.r_attr + (size_t)(i0 + lr) * cx.Fp, cx.om, cx.Fp);
   const bool act = t < s.R * s.n_col;
@@ -1090,16 +1098,27 @@ __device__ __noinline__ void run_pair_c(const Ctx& cx, const Geo& g, const Group
   float sk = 1.f;
   for (int k = 0; k < cx.K; ++k) {
     const ClusterY cur{(k & 1) ? 4u * (uint32_t)nn : 0u};
+    const char* lcur = reinterpret_cast<const char*>((k & 1) ? buf1 : buf0);
     float* nxt = (k & 1) ? buf0 : buf1;
     const float ca = 0.5f * cx.alpha * sk;
     ss = 0.f;
     for (int m = 0, lr = r0, off = off0; m < Mt; ++m, lr += s.R, off += step) {
       const int4 A = ra[lr], Q = rq[lr];
-      float z = gather_fast(cur, A, Q, cl);
-      if (A.w < 0 || cl.flag) {
-        const int4 R4 = rr[lr];
-        if (A.w < 0) z += row_extra(cur, R4, redge, cl);
-        if (cl.flag) z += col_extra(cur, A, Q, R4, redge, cedge, cl);
+      float z;
+      if (A.y >= 0) {  // every neighbour row in this CTA: plain shared loads
+        z = gather_fast(lcur, A, Q, cl);
+        if (A.w < 0 || cl.flag) {
+          const int4 R4 = rr[lr];
+          if (A.w < 0) z += row_extra(lcur, R4, redge, cl);
+          if (cl.flag) z += col_extra(lcur, A, Q, R4, redge, cedge, cl);
+        }
+      } else {
+        z = gather_fast(cur, A, Q, cl);
+        if (A.w < 0 || cl.flag) {
+          const int4 R4 = rr[lr];
+          if (A.w < 0) z += row_extra(cur, R4, redge, cl);
+          if (cl.flag) z += col_extra(cur, A, Q, R4, redge, cedge, cl);
+        }
       }
       const float y = fmaf(ca, z, ehb[off]);
       nxt[off] = y;
@@ -1120,11 +1139,14 @@ __device__ __noinline__ void run_pair_c(const Ctx& cx, const Geo& g, const Group
     if (xo) xo[s.tr ? (size_t)j * s.n_row + i : (size_t)i * s.n_col + j] = x;
   }
   cl_sync();  // the whole X_K is in the slot
-  if (rank == 0 && (cx.scores || cx.match)) {
+  if (cx.scores || cx.match) {
+    // the greedy rounds on the whole cluster: rows and columns spread over
+    // every warp of every CTA, the matching state in the slot
+    const ClGroup cg{rank * G + t, C * G, C, &st};
     int32_t* ms = reinterpret_cast<int32_t*>(slot + (size_t)s.n_row * s.n_col);
     int32_t* mo = cx.match ? cx.match + cx.m_off[g.p] : nullptr;
-    const float sc = greedy<int32_t>(grp, slot, s.n_col, s.n_row, s.n_col, s.tr, ms, ms + s.n_row, mo, cx.hdr, g.p);
-    if (cx.scores && t == 0) cx.scores[g.p] = sc;
+    const float sc = greedy<int32_t>(cg, slot, s.n_col, s.n_row, s.n_col, s.tr, ms, ms + s.n_row, mo, cx.hdr, g.p);
+    if (cx.scores && cg.rank == 0) cx.scores[g.p] = sc;
   }
 }
 
@@ -1161,6 +1183,7 @@ __global__ void __launch_bounds__(NT, 1) fwd_cluster_kernel(CallArgs a) {
   if (t < C) {
     st.rbase[t] = cl_map(smem, t);
     st.paddr[t] = cl_map(st.part, t);
+    st.piaddr[t] = cl_map(st.parti, t);
   }
   if (t == 0) st.qaddr = cl_map(&st.q, 0);
   __syncthreads();

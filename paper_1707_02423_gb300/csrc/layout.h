@@ -216,8 +216,10 @@ struct WsHeader {
   uint32_t n_class[kNumClasses];
   uint64_t slot_need;      // bytes of scratch the largest global-class pair needs
   uint64_t bwd_slot_need;  // bytes of adjoint scratch the largest pair needs
-  uint32_t q_bwd;          // adjoint work counter
+  uint32_t q_bwd;          // adjoint work counter (one-CTA pairs)
   uint32_t q_opt;          // optimal-matching work counter
+  uint32_t q_bwd_big;      // adjoint work counter (pairs on clusters)
+  uint32_t pad_;
   uint32_t hist[kNumClasses][kBuckets];
   uint32_t cursor[kNumClasses][kBuckets];
   int64_t x_total, m_total;
