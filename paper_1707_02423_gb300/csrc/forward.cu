@@ -486,7 +486,8 @@ __device__ __forceinline__ float greedy_ranked(const Group& grp, const float* X,
 
 // Write X_K (resident, possibly transposed, stride ld) to the caller's
 // row-major n_a x n_b output, coalesced on the global side.
-__device__ __forceinline__ void store_x(const Group& grp, const Ctx& cx, const Geo& g, const float* Xs, int ld) {
+template <class Grp>
+__device__ __forceinline__ void store_x(const Grp& grp, const Ctx& cx, const Geo& g, const float* Xs, int ld) {
   float* dst = cx.X + cx.x_off[g.p];
   const int tot = g.na * g.nb;
   for (int idx = grp.rank; idx < tot; idx += grp.size) {
@@ -648,16 +649,17 @@ __device__ __forceinline__ void for_entries(int n_row, int n_col, int ld, int t,
   }
 }
 
-// A global-class pair on the whole CTA (too large for shared memory): the
-// iterates, (1-alpha) Ehat and the matching state live in a scratch slot of
-// the workspace (L2-resident); the row and column graphs are staged in the
-// CTA's shared memory exactly as for a resident pair, and the gather is the
-// same straight-line code on global addresses.  Columns are spread over
-// C = min(n_col, NT) lanes and rows over NT / C row groups; a thread loops
-// over its columns and rows.  Slot: [ehb | buf0 | buf1] (n_row x n_col
-// floats each), row norms, int32 matching state.
-template <bool kStaged>
-__device__ __noinline__ void run_pair_g(const Ctx& cx, const Geo& g, const Group& grp, float* slot,
+// A global-class pair (too large for shared memory) on a team -- the whole
+// CTA, or every CTA of a thread-block cluster: the iterates, (1-alpha) Ehat
+// and the matching state live in a scratch slot of the workspace
+// (L2-resident); each CTA stages the row and column graphs in its own shared
+// memory exactly as for a resident pair, and the gather is the same
+// straight-line code on global addresses.  The team sweeps the entries in
+// row-major order (team rank t takes t, t + G, ...).  Slot: [ehb | buf0 |
+// buf1] (n_row x n_col floats each), row norms, int32 matching state.
+// loc: this CTA (for the staging); team: the threads sharing the pair.
+template <bool kStaged, class Grp>
+__device__ __noinline__ void run_pair_g(const Ctx& cx, const Geo& g, const Group& loc, const Grp& grp, float* slot,
                                         unsigned char* region) {
   const int n_row = g.na, n_col = g.nb, ld = g.nb;  // global-class shapes are never transposed
   const size_t E = (size_t)n_row * n_col;
@@ -680,9 +682,9 @@ __device__ __noinline__ void run_pair_g(const Ctx& cx, const Geo& g, const Group
   const int e_col = __ldg(g.c_optr + n_col) - co0;
   int2* cedge = redge + 2 * e_row;
   int* cptr = reinterpret_cast<int*>(cedge + 2 * e_col);
-  if (!kStaged)
-    for (int i = t; i < n_row; i += G) rn[i] = attr_norm(g.r_attr + (size_t)i * cx.Fp, cx.om, cx.Fp);
-  for (int i = t; kStaged && i < n_row; i += G) {
+  for (int i = t; i < n_row; i += G) rn[i] = attr_norm(g.r_attr + (size_t)i * cx.Fp, cx.om, cx.Fp);
+  const int lt = loc.rank, LG = loc.size;
+  for (int i = lt; kStaged && i < n_row; i += LG) {
     const int o0 = __ldg(g.r_optr + i) - eo0, o1 = __ldg(g.r_optr + i + 1) - eo0;
     const int q0 = __ldg(g.r_iptr + i) - ei0, q1 = __ldg(g.r_iptr + i + 1) - ei0;
     const CfAdj z{0, 0.f};
@@ -692,26 +694,25 @@ __device__ __noinline__ void run_pair_g(const Ctx& cx, const Geo& g, const Group
     ra[i] = make_int4(4 * ld * a0.nbr, __float_as_int(a0.w), 4 * ld * a1.nbr, __float_as_int(a1.w) | flag);
     rq[i] = make_int4(4 * ld * b0.nbr, __float_as_int(b0.w), 4 * ld * b1.nbr, __float_as_int(b1.w));
     rr[i] = make_int4(o0, o1, e_row + q0, e_row + q1);
-    rn[i] = attr_norm(g.r_attr + (size_t)i * cx.Fp, cx.om, cx.Fp);
   }
-  for (int k = t; kStaged && k < e_row; k += G) {
+  for (int k = lt; kStaged && k < e_row; k += LG) {
     const CfAdj a = ldg_adj(g.r_oadj + eo0 + k), b = ldg_adj(g.r_iadj + ei0 + k);
     redge[k] = make_int2(4 * ld * a.nbr, __float_as_int(a.w));
     redge[e_row + k] = make_int2(4 * ld * b.nbr, __float_as_int(b.w));
   }
-  for (int k = t; kStaged && k < e_col; k += G) {
+  for (int k = lt; kStaged && k < e_col; k += LG) {
     const CfAdj a = ldg_adj(g.c_oadj + co0 + k), b = ldg_adj(g.c_iadj + ci0 + k);
     cedge[k] = make_int2(4 * a.nbr, __float_as_int(a.w));
     cedge[e_col + k] = make_int2(4 * b.nbr, __float_as_int(b.w));
   }
-  for (int k = t; kStaged && k <= n_col; k += G) {
+  for (int k = lt; kStaged && k <= n_col; k += LG) {
     cptr[k] = __ldg(g.c_optr + k) - co0;
     cptr[n_col + 1 + k] = e_col + __ldg(g.c_iptr + k) - ci0;
   }
-  grp.sync();
+  grp.sync();  // staged lists (this CTA) and row norms (the team) visible
 
-  // Entries are visited in row-major order, thread t taking t, t + G, ...:
-  // the whole CTA sweeps a narrow band of rows at a time, so the rows its
+  // Entries are visited in row-major order, team thread t taking t, t + G,
+  // ...: the team sweeps a narrow band of rows at a time, so the rows its
   // gathers read (neighbours of the band) stay cache-resident.  (i, j) of the
   // next entry follow without a division.
 
@@ -849,8 +850,9 @@ __global__ void __launch_bounds__(NT, 1) fwd_batched_kernel(CallArgs a, int per_
 
   uint32_t n[kNumClasses];
   for (int c = 0; c < kNumClasses; ++c) n[c] = single ? 0u : cx.hdr->n_class[c];
-  // global class: whole CTA, one scratch slot per CTA
-  if (n[kClassGlobal] > 0) {
+  // global class: whole CTA, one scratch slot per CTA (with the cluster tier
+  // on, the cluster kernel has run these pairs)
+  if (n[kClassGlobal] > 0 && a.cluster < 2) {
     const uint64_t need = cx.hdr->slot_need;
     const uint64_t nslots = need ? cx.scratch_bytes / need : 0;
     if (nslots == 0) {
@@ -866,9 +868,9 @@ __global__ void __launch_bounds__(NT, 1) fwd_batched_kernel(CallArgs a, int per_
         {
           const Geo g = make_geo(cx, (int)cx.queue[q], cc);
           if (staged_fits(g, cc.z_cta))
-            run_pair_g<true>(cx, g, cta, slot, smem);
+            run_pair_g<true>(cx, g, cta, cta, slot, smem);
           else
-            run_pair_g<false>(cx, g, cta, slot, smem);
+            run_pair_g<false>(cx, g, cta, cta, slot, smem);
         }
       }
     }
@@ -906,9 +908,9 @@ __global__ void __launch_bounds__(NT, 1) fwd_batched_kernel(CallArgs a, int per_
           if (t == 0) set_status(cx.hdr, 2 /* CF_ERR_WORKSPACE */, per_pair);
         } else {
           if (staged_fits(g, cc.z_cta))
-            run_pair_g<true>(cx, g, cta, reinterpret_cast<float*>(cx.scratch), smem);
+            run_pair_g<true>(cx, g, cta, cta, reinterpret_cast<float*>(cx.scratch), smem);
           else
-            run_pair_g<false>(cx, g, cta, reinterpret_cast<float*>(cx.scratch), smem);
+            run_pair_g<false>(cx, g, cta, cta, reinterpret_cast<float*>(cx.scratch), smem);
         }
         break;
       }
@@ -1168,8 +1170,8 @@ __global__ void __launch_bounds__(NT, 1) fwd_cluster_kernel(CallArgs a) {
   const int t = threadIdx.x;
   const int C = (int)cl_size(), rank = (int)cl_rank();
   const uint32_t cid = cl_index();
-  const uint32_t n_cl = cx.hdr->n_class[kClassCluster];
-  if (n_cl == 0) return;
+  const uint32_t n_cl = cx.hdr->n_class[kClassCluster], n_gl = cx.hdr->n_class[kClassGlobal];
+  if (n_cl == 0 && n_gl == 0) return;
   const uint64_t need = cx.hdr->slot_need;
   const uint64_t nslots = need ? cx.scratch_bytes / need : 0;
   if (nslots == 0) {
@@ -1189,6 +1191,21 @@ __global__ void __launch_bounds__(NT, 1) fwd_cluster_kernel(CallArgs a) {
   __syncthreads();
   float* slot = reinterpret_cast<float*>(cx.scratch + (size_t)cid * need);
   const Group cta{t, NT, 0, s_redf, s_redi};
+  // the global class (too large for the cluster's shared memory): the whole
+  // cluster sweeps the pair's L2-resident slot
+  const ClGroup team{rank * NT + t, C * NT, C, &st};
+  for (;;) {
+    if (rank == 0 && t == 0) st.q = atomicAdd(&cx.hdr->q_next[kClassGlobal], 1u);
+    cl_sync();
+    const uint32_t q = cl_ld_u32(st.qaddr);
+    cl_sync();  // CTA 0 overwrites q only after every CTA has read it
+    if (q >= n_gl) break;
+    const Geo g = make_geo(cx, (int)cx.queue[q], cc);
+    if (staged_fits(g, cc.z_cta))
+      run_pair_g<true>(cx, g, cta, team, slot, smem);
+    else
+      run_pair_g<false>(cx, g, cta, team, slot, smem);
+  }
   for (;;) {
     if (rank == 0 && t == 0) st.q = atomicAdd(&cx.hdr->q_next[kClassCluster], 1u);
     cl_sync();

@@ -32,12 +32,12 @@ def _built():
 
 
 def compare(cfgs_a, cfgs_b, pairs, F, omega=None, alpha=0.8, K=40, per_pair=False, norm_mode=0,
-            check_x=True, sample=None):
+            check_x=True, sample=None, tune=0):
     pa = api.Pack(cfgs_a, F, device=DEV)
     pb = pa if cfgs_b is cfgs_a else api.Pack(cfgs_b, F, device=DEV)
     om = np.ones(F) if omega is None else np.asarray(omega, np.float64)
     res = api.similarity(pa, pb, pairs, torch.tensor(om, dtype=torch.float32, device=DEV), alpha, K,
-                         want_x=check_x, want_match=True, per_pair=per_pair, norm_mode=norm_mode)
+                         want_x=check_x, want_match=True, per_pair=per_pair, norm_mode=norm_mode, tune=tune)
     scores = res.scores.cpu().numpy()
     match = res.match.cpu().numpy()
     X = res.X.cpu().numpy() if check_x else None
@@ -156,9 +156,10 @@ def test_query_shape_f25():
     compare(w.cfgs_a, w.cfgs_b, w.pairs, w.F)
 
 
-def test_large_cfgs_global_class():
+@pytest.mark.parametrize("tune", [0, 1 + 18 * 2, 1 + 18 * 3])  # one CTA per pair; 4- and 8-CTA cluster teams
+def test_large_cfgs_global_class(tune):
     w = config3(3, 500, 900)
-    compare(w.cfgs_a, w.cfgs_a, w.pairs, w.F)
+    compare(w.cfgs_a, w.cfgs_a, w.pairs, w.F, tune=tune)
 
 
 def test_full_cfg2_sampled():
