@@ -180,6 +180,25 @@ def dist_setup(n_gpus):
     return world, rank, local
 
 
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The slowest rank's figure (the job's time) when several ranks run."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(pairs_per_rank: int, world: int, ms_per_step: float) -> float:
+    """Whole-job pairs/s: every rank runs its own replica of the workload
+    (pairs are independent; no data-path collective), so the job completes
+    world x pairs in the slowest rank's step time."""
+    return world * pairs_per_rank / (ms_per_step * 1e-3)
+
+
 def run_reference(args):
     """The reference arm: the FP64 CPU oracle, timed on the host cores."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -308,18 +327,12 @@ def run_workload(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     with ClockSampler(local) as clk:
         ms = timed_steps(step, args.steps, args.warmup, flush, stream)
-    tot = float(sum(ms))
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([tot], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot = float(t.item())
+    tot = max_over_ranks(float(sum(ms)), world, dev)
     if rank != 0:
         return
     mps = tot / args.steps
     print(json.dumps({
-        "metric": METRIC, "value": world * P / (mps * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": job_rate(P, world, mps), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "pairs": P,
@@ -398,17 +411,10 @@ def run_ours(args):
         t_wall = time.perf_counter() - t_wall
     step_ms = [e[0].elapsed_time(e[2]) for e in ev]
     fwd_ms = [e[1].elapsed_time(e[2]) for e in ev]
-    tot_ms = float(sum(step_ms))
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-        dist.barrier()
+    tot_ms = max_over_ranks(float(sum(step_ms)), world, dev)
     B.check(B.lib().cf_status_check(ws.get(ws_bytes).data_ptr(), int(stream.cuda_stream)))
     ms_per_step = tot_ms / args.steps
-    value = world * P / (ms_per_step * 1e-3)
+    value = job_rate(P, world, ms_per_step)
 
     # ---- per-pair form: one launch per pair, same math
     pp_steps = 2
