@@ -123,6 +123,7 @@ cf_status build_pack(const cf_cfg_view* cfgs, int32_t n_cfgs, int32_t F, void* o
   h.off_in_eid = take(4 * (size_t)std::max<int64_t>(n_edges, 1));
   h.off_u2c = take(4 * (size_t)std::max<int64_t>(n_user, 1));
   h.off_attr = take(4 * (size_t)n_blocks * F_pad);
+  h.off_xdeg = take((size_t)n_cfgs);
   h.total_bytes = (int64_t)o;
   *bytes_needed = o;
   if (!out) return ok();
@@ -140,6 +141,7 @@ cf_status build_pack(const cf_cfg_view* cfgs, int32_t n_cfgs, int32_t F, void* o
   int32_t* in_eid = reinterpret_cast<int32_t*>(base + h.off_in_eid);
   int32_t* u2c = reinterpret_cast<int32_t*>(base + h.off_u2c);
   float* attr = reinterpret_cast<float*>(base + h.off_attr);
+  uint8_t* xdeg = reinterpret_cast<uint8_t*>(base + h.off_xdeg);
 
   int32_t nb = 0, ne = 0, nu = 0;
   int max_out = 0, max_in = 0;
@@ -170,11 +172,14 @@ cf_status build_pack(const cf_cfg_view* cfgs, int32_t n_cfgs, int32_t F, void* o
       out_adj[ne + k] = CfAdj{ddst[k], dw[k]};
     }
     int32_t run = ne;
+    uint8_t busy = 0;
     for (int i = 0; i < v.n_blocks; ++i) {
       out_ptr[nb + i] = run;
       run += outdeg[i];
       max_out = std::max(max_out, outdeg[i]);
+      busy |= (outdeg[i] > 2 || indeg[i] > 2) ? 1 : 0;
     }
+    xdeg[c] = busy;
     std::vector<int32_t> by_dst(d);
     std::iota(by_dst.begin(), by_dst.end(), 0);
     std::stable_sort(by_dst.begin(), by_dst.end(), [&](int32_t x, int32_t y) {
@@ -262,6 +267,8 @@ cf_status scan_pairs(const void* h_pack_a, const void* h_pack_b, const int32_t* 
   const int32_t* nob = reinterpret_cast<const int32_t*>(static_cast<const char*>(h_pack_b) + hb.off_node);
   const int32_t* eoa = reinterpret_cast<const int32_t*>(static_cast<const char*>(h_pack_a) + ha.off_edge);
   const int32_t* eob = reinterpret_cast<const int32_t*>(static_cast<const char*>(h_pack_b) + hb.off_edge);
+  const uint8_t* xda = reinterpret_cast<const uint8_t*>(static_cast<const char*>(h_pack_a) + ha.off_xdeg);
+  const uint8_t* xdb = reinterpret_cast<const uint8_t*>(static_cast<const char*>(h_pack_b) + hb.off_xdeg);
   int64_t xs = 0, ms = 0, ng = 0;
   size_t need = 0;
   // pairs that fit no single CTA: the global class, or the cluster class under a tune with clusters
@@ -273,7 +280,7 @@ cf_status scan_pairs(const void* h_pack_a, const void* h_pack_b, const int32_t* 
     const int na = noa[a + 1] - noa[a], nb = nob[b + 1] - nob[b];
     xs += (int64_t)na * nb;
     ms += na;
-    if (classify(na, nb, eoa[a + 1] - eoa[a], eob[b + 1] - eob[b], cc).cls == kClassGlobal) {
+    if (classify(na, nb, eoa[a + 1] - eoa[a], eob[b + 1] - eob[b], cc, xda[a], xdb[b]).cls == kClassGlobal) {
       need = std::max(need, global_slot_bytes(na, nb));
       ++ng;
     }

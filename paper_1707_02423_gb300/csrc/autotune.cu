@@ -237,25 +237,28 @@ cf_status cf_autotune(const void* h_pack_a, const void* h_pack_b, const void* d_
     if (e0) cudaEventDestroy(e0);
     return tfail(CF_ERR_CUDA, "autotune events");
   }
+  // one timed call of cf_similarity under `tune` on the first n sample pairs
+  auto timed = [&](int tune_id, int n, float* ms) -> cf_status {
+    cf_params p = *params;
+    p.flags = 0;
+    p.tune = tune_id;
+    cudaEventRecord(e0, st);
+    cf_status r = cf_similarity(d_pack_a, d_pack_b, d_pairs, n, &p, d_omega, nullptr, d_scores, d_match, d_ws,
+                                L.sim_ws, stream);
+    if (r) return r;
+    cudaEventRecord(e1, st);
+    const cudaError_t ce = cudaEventSynchronize(e1);
+    if (ce != cudaSuccess) return tfail(CF_ERR_CUDA, "autotune run: %s", cudaGetErrorString(ce));
+    cudaEventElapsedTime(ms, e0, e1);
+    return CF_OK;
+  };
   // if one call of the default tune on the sample exceeds the time budget,
   // time the candidates on an evenly strided part of the sample that fits it
   int St = S;
-  for (int once = 0; once < 1; ++once) {
-    cf_params p = *params;
-    p.flags = 0;
-    p.tune = 1;
-    cudaEventRecord(e0, st);
-    s = cf_similarity(d_pack_a, d_pack_b, d_pairs, St, &p, d_omega, nullptr, d_scores, d_match, d_ws, L.sim_ws, stream);
-    if (s) break;
-    cudaEventRecord(e1, st);
-    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
-      s = tfail(CF_ERR_CUDA, "autotune run: %s", cudaGetErrorString(e));
-      break;
-    }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms <= kTuneBudgetMs || St <= kTuneMinPairs) break;
-    const int S2 = std::max(kTuneMinPairs, (int)(St * (kTuneBudgetMs / ms)));
+  float ms0 = 0.f;
+  s = timed(1, St, &ms0);
+  if (s == CF_OK && ms0 > kTuneBudgetMs && St > kTuneMinPairs) {
+    const int S2 = std::max(kTuneMinPairs, (int)(St * (kTuneBudgetMs / ms0)));
     std::vector<int32_t> sub(2 * (size_t)S2);
     for (int k = 0; k < S2; ++k) {
       const int64_t q = (int64_t)k * St / S2;
@@ -263,31 +266,17 @@ cf_status cf_autotune(const void* h_pack_a, const void* h_pack_b, const void* d_
       sub[2 * k + 1] = sp[2 * q + 1];
     }
     if ((e = cudaMemcpyAsync(d_pairs, sub.data(), 8 * (size_t)S2, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
       s = tfail(CF_ERR_CUDA, "autotune pair upload: %s", cudaGetErrorString(e));
-      break;
-    }
     St = S2;
   }
   int best_t = 0;
   float best = 1e30f;
   for (int t = 1; t <= kNumTunes && s == CF_OK; ++t) {
-    cf_params p = *params;
-    p.flags = 0;
-    p.tune = t;
     float tmin = 1e30f;
-    for (int r = 0; r <= kTuneReps && s == CF_OK; ++r) {
-      cudaEventRecord(e0, st);
-      s = cf_similarity(d_pack_a, d_pack_b, d_pairs, St, &p, d_omega, nullptr, d_scores, d_match, d_ws, L.sim_ws,
-                        stream);
-      if (s) break;
-      cudaEventRecord(e1, st);
-      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
-        s = tfail(CF_ERR_CUDA, "autotune run: %s", cudaGetErrorString(e));
-        break;
-      }
+    for (int r = 0; r <= kTuneReps && s == CF_OK; ++r) {  // call 0 warms up
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
+      s = timed(t, St, &ms);
       if (r > 0) tmin = std::min(tmin, ms);
     }
     if (s == CF_OK) s = cf_status_check(d_ws, stream);

@@ -21,6 +21,7 @@ struct PackView {
   const int32_t* in_eid;
   const int32_t* u2c;
   const float* attr;
+  const uint8_t* xdeg;
   int n_cfgs, F, F_pad;
 };
 
@@ -38,6 +39,7 @@ __device__ __forceinline__ PackView load_pack(const void* base) {
   v.in_eid = reinterpret_cast<const int32_t*>(b + h->off_in_eid);
   v.u2c = reinterpret_cast<const int32_t*>(b + h->off_u2c);
   v.attr = reinterpret_cast<const float*>(b + h->off_attr);
+  v.xdeg = reinterpret_cast<const uint8_t*>(b + h->off_xdeg);
   v.n_cfgs = h->n_cfgs;
   v.F = h->F;
   v.F_pad = h->F_pad;

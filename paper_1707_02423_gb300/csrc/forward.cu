@@ -76,7 +76,7 @@ __device__ __forceinline__ Geo make_geo(const Ctx& cx, int p, const ClassCfg& cc
   g.nb = __ldg(cx.B.node_off + pb + 1) - bb;
   const int ea = __ldg(cx.A.edge_off + pa + 1) - __ldg(cx.A.edge_off + pa);
   const int eb = __ldg(cx.B.edge_off + pb + 1) - __ldg(cx.B.edge_off + pb);
-  g.s = classify(g.na, g.nb, ea, eb, cc);
+  g.s = classify(g.na, g.nb, ea, eb, cc, __ldg(cx.A.xdeg + pa), __ldg(cx.B.xdeg + pb));
   const PackView& R = g.s.tr ? cx.B : cx.A;
   const PackView& C = g.s.tr ? cx.A : cx.B;
   const int rb = g.s.tr ? bb : ba, cbse = g.s.tr ? ba : bb;

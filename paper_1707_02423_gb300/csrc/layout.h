@@ -16,7 +16,7 @@
 namespace cfsim {
 
 constexpr uint32_t kPackMagic = 0x4B504643u;  // "CFPK"
-constexpr uint32_t kPackVersion = 1;
+constexpr uint32_t kPackVersion = 2;
 constexpr int kMaxBlocks = 32000;  // per CFG; matching state packs indices in int16
 constexpr int kMaxF = 32;          // attributes per block
 constexpr size_t kAlign = 256;
@@ -46,6 +46,7 @@ struct PackHeader {
   int64_t off_in_eid;   // int32 [n_edges] distinct-edge id of each in_adj entry
   int64_t off_u2c;      // int32 [n_user_edges] distinct-edge id of each user edge
   int64_t off_attr;     // float [n_blocks * F_pad]
+  int64_t off_xdeg;     // uint8 [n_cfgs]: 1 if a block has more than two out- or in-neighbours
 };
 
 // Execution classes of a pair, in queue order: the global-memory tier, the
@@ -114,9 +115,21 @@ CF_HD size_t group_region(int cls, const ClassCfg& c) {
   return (size_t)(cls == kClassWarp ? c.z_wrp : cls == kClassQuarter ? c.z_qtr : c.z_cta);
 }
 
+// Orientation of a pair that fits both ways: the column graph's lists live in
+// each thread's registers (its first two neighbours) and a column with more
+// than two neighbours makes its lane run extra work while the rest of its warp
+// waits, whereas a row's further neighbours are handled by whole warps.  So a
+// CFG with such blocks (xa / xb) goes to the row side when the other has none;
+// otherwise fewest rows per thread (ties: untransposed).
+CF_HD bool prefer_tr(int M0, int M1, int xa, int xb) {
+  if ((xa != 0) != (xb != 0)) return xb != 0;  // B has the busy blocks: make B the row graph
+  return M1 < M0;
+}
+
 // Smallest group level (not below c.min_cls) whose region holds the pair,
-// with the orientation of fewest rows per thread (ties: untransposed).
-CF_HD Shape classify(int na, int nb, int ea, int eb, const ClassCfg& c) {
+// oriented by prefer_tr.  xa / xb: whether CFG A / B has a block with more
+// than two out- or in-neighbours.
+CF_HD Shape classify(int na, int nb, int ea, int eb, const ClassCfg& c, int xa = 0, int xb = 0) {
   Shape s{};
   for (int cls = c.min_cls; cls >= kClassCta; --cls) {
     const int G = group_size(cls, c);
@@ -125,7 +138,7 @@ CF_HD Shape classify(int na, int nb, int ea, int eb, const ClassCfg& c) {
     const bool f0 = fits(na, nb, ea, eb, G, Z, &R0, &M0);
     const bool f1 = fits(nb, na, eb, ea, G, Z, &R1, &M1);
     if (f0 || f1) {
-      const bool tr = !f0 || (f1 && M1 < M0);
+      const bool tr = !f0 || (f1 && prefer_tr(M0, M1, xa, xb));
       s.cls = cls;
       s.tr = tr ? 1 : 0;
       s.n_row = tr ? nb : na;
@@ -146,7 +159,7 @@ CF_HD Shape classify(int na, int nb, int ea, int eb, const ClassCfg& c) {
     if (f0) M0 = ceil_div(s0, c.nt / nb);
     if (f1) M1 = ceil_div(s1, c.nt / na);
     if (f0 || f1) {
-      const bool tr = !f0 || (f1 && M1 < M0);
+      const bool tr = !f0 || (f1 && prefer_tr(M0, M1, xa, xb));
       s.cls = kClassCluster;
       s.tr = tr ? 1 : 0;
       s.n_row = tr ? nb : na;

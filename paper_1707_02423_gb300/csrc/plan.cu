@@ -62,7 +62,7 @@ __device__ __forceinline__ PairFacts pair_facts(const PlanCtx& c, int p, const C
   const int eb = __ldg(c.B.edge_off + pb + 1) - __ldg(c.B.edge_off + pb);
   f.ea = ea;
   f.eb = eb;
-  Shape s = classify(f.na, f.nb, ea, eb, cc);
+  Shape s = classify(f.na, f.nb, ea, eb, cc, __ldg(c.A.xdeg + pa), __ldg(c.B.xdeg + pb));
   f.cls = s.cls;
   // per-iteration work: every entry is written once, every edge pair gathered twice
   f.bucket = cost_bucket((int64_t)f.na * f.nb + 2 * (int64_t)ea * eb);

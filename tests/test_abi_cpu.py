@@ -64,7 +64,8 @@ HDR = np.dtype([("magic", "<u4"), ("version", "<u4"), ("n_cfgs", "<i4"), ("F", "
                 ("max_blocks", "<i4"), ("max_out", "<i4"), ("max_in", "<i4"), ("n_blocks", "<i8"),
                 ("n_edges", "<i8"), ("n_user", "<i8"), ("total", "<i8"), ("off_node", "<i8"), ("off_edge", "<i8"),
                 ("off_uedge", "<i8"), ("off_out_ptr", "<i8"), ("off_in_ptr", "<i8"), ("off_out_adj", "<i8"),
-                ("off_in_adj", "<i8"), ("off_in_eid", "<i8"), ("off_u2c", "<i8"), ("off_attr", "<i8")])
+                ("off_in_adj", "<i8"), ("off_in_eid", "<i8"), ("off_u2c", "<i8"), ("off_attr", "<i8"),
+                ("off_xdeg", "<i8")])
 
 
 def parse(buf):
@@ -83,6 +84,7 @@ def parse(buf):
         "out_adj": arr(h["off_out_adj"], adj, ne), "in_adj": arr(h["off_in_adj"], adj, ne),
         "in_eid": arr(h["off_in_eid"], "<i4", ne), "u2c": arr(h["off_u2c"], "<i4", nu),
         "attr": arr(h["off_attr"], "<f4", nb * int(h["F_pad"])).reshape(nb, int(h["F_pad"])),
+        "xdeg": arr(h["off_xdeg"], "<u1", nc),
     }
 
 
@@ -97,7 +99,8 @@ def test_pack_layout_matches_the_graphs(L):
     P = parse(buf)
     h = P["h"]
     assert h["magic"] == 0x4B504643 and h["F"] == 13 and h["F_pad"] == 16
-    for off in ("off_node", "off_out_ptr", "off_out_adj", "off_attr", "off_u2c"):
+    assert h["version"] == 2
+    for off in ("off_node", "off_out_ptr", "off_out_adj", "off_attr", "off_u2c", "off_xdeg"):
         assert h[off] % 256 == 0
     for c, g in enumerate(cfgs):
         b0, b1 = P["node"][c], P["node"][c + 1]
@@ -121,6 +124,11 @@ def test_pack_layout_matches_the_graphs(L):
             assert P["out_adj"][d]["nbr"] == g.dst[e]
             assert P["out_ptr"][b0 + g.src[e]] <= d < P["out_ptr"][b0 + g.src[e] + 1]
         assert np.array_equal(P["attr"][b0:b1, :13], g.attr) and not P["attr"][b0:b1, 13:].any()
+        # the per-CFG flag: some block with more than two distinct out- or in-neighbours
+        es = set(zip(g.src.tolist(), g.dst.tolist()))
+        od = np.bincount([a for a, _ in es], minlength=g.n)
+        idg = np.bincount([b for _, b in es], minlength=g.n)
+        assert P["xdeg"][c] == int(od.max() > 2 or idg.max() > 2)
     info = B.cf_pack_info()
     B.check(L.cf_pack_info_get(buf.ctypes.data, C.byref(info)))
     assert info.n_cfgs == 12 and info.n_user_edges == sum(len(c.src) for c in cfgs)
