@@ -46,7 +46,8 @@ struct Ctx {
   WsHeader* hdr;
   unsigned char* scratch;
   size_t scratch_bytes;
-  const float* om;  // omega, shared-memory copy
+  const float* om;    // omega, shared-memory copy
+  const float* sqom;  // sqrt(omega), shared-memory copy
   int F, Fp;
   int ranked;  // matching policy (ClassCfg::ranked)
 };
@@ -138,13 +139,11 @@ struct Group {
 
 // Lists of one column-graph block j for the straight-line gather: its first
 // two out- and in-neighbours as byte offsets v * 4 with weights, missing
-// entries padded with {0, 0.0f}; the ranges of its further neighbours in the
-// staged column entries (empty for the common degree <= 2); flag != 0 when
-// there are any.
+// entries padded with {0, 0.0f}; flag != 0 when it has further neighbours
+// (col_extra then reads their ranges from the staged row pointers).
 struct ColPad {
   int vo0, vo1, vi0, vi1;
   float wo0, wo1, wi0, wi1;
-  int xo0, xo1, xi0, xi1;
   int flag;
 };
 
@@ -159,8 +158,6 @@ __device__ __forceinline__ ColPad load_col(const int* cptr, const int2* cedge, i
   x = e1 > e0 + 1 ? cedge[e0 + 1] : make_int2(0, 0);
   c.vo1 = x.x;
   c.wo1 = __int_as_float(x.y);
-  c.xo0 = e0 + 2;
-  c.xo1 = e1;
   const int f0 = cptr[n_col + 1 + j], f1 = cptr[n_col + 2 + j];
   x = f1 > f0 ? cedge[f0] : make_int2(0, 0);
   c.vi0 = x.x;
@@ -168,8 +165,6 @@ __device__ __forceinline__ ColPad load_col(const int* cptr, const int2* cedge, i
   x = f1 > f0 + 1 ? cedge[f0 + 1] : make_int2(0, 0);
   c.vi1 = x.x;
   c.wi1 = __int_as_float(x.y);
-  c.xi0 = f0 + 2;
-  c.xi1 = f1;
   c.flag = (e1 - e0 > 2 || f1 - f0 > 2) ? 1 : 0;
   return c;
 }
@@ -231,11 +226,13 @@ __device__ __forceinline__ float row_extra(YT Y, const int4 rr, const int2* redg
 }
 
 // cedge = the column graph's staged {v 4, w} entries (out-edges, then in-edges).
+// cptr / n_col / j locate column j's further neighbours in cedge.
 template <class YT>
 __device__ __forceinline__ float col_extra(YT Y, const int4 A, const int4 Q, const int4 rr, const int2* redge,
-                                           const int2* cedge, const ColPad& c) {
+                                           const int2* cedge, const int* cptr, int n_col, int j) {
   float s = 0.f;
-  for (int f = c.xo0; f < c.xo1; ++f) {
+  const int xo1 = cptr[j + 1], xi0 = cptr[n_col + 1 + j] + 2, xi1 = cptr[n_col + 2 + j];
+  for (int f = cptr[j] + 2; f < xo1; ++f) {
     const int2 v = cedge[f];
     float t = fmaf(fabsf(__int_as_float(A.w)), lds_at(Y, A.z, v.x), fabsf(__int_as_float(A.y)) * lds_at(Y, A.x, v.x));
     for (int k = rr.x + 2; k < rr.y; ++k) {
@@ -244,7 +241,7 @@ __device__ __forceinline__ float col_extra(YT Y, const int4 A, const int4 Q, con
     }
     s = fmaf(__int_as_float(v.y), t, s);
   }
-  for (int f = c.xi0; f < c.xi1; ++f) {
+  for (int f = xi0; f < xi1; ++f) {
     const int2 v = cedge[f];
     float t = fmaf(__int_as_float(Q.w), lds_at(Y, Q.z, v.x), __int_as_float(Q.y) * lds_at(Y, Q.x, v.x));
     for (int k = rr.z + 2; k < rr.w; ++k) {
@@ -497,6 +494,28 @@ __device__ __forceinline__ void store_x(const Grp& grp, const Ctx& cx, const Geo
   }
 }
 
+// Unit attribute vector of one block: a_f sqrt(omega_f) / r with
+// r = sqrt(sum_f omega_f a_f^2), zero when r = 0, so that the cosine term of
+// two blocks is the plain dot product of their unit vectors.  sq = sqrt(omega)
+// (shared memory), Fp floats in and out.
+__device__ __forceinline__ void unit_attr(const float* a, const float* sq, int Fp, float* out) {
+  const float4* a4 = reinterpret_cast<const float4*>(a);
+  const float4* s4 = reinterpret_cast<const float4*>(sq);
+  float4* o4 = reinterpret_cast<float4*>(out);
+  float acc = 0.f;
+  for (int q = 0; q < (Fp >> 2); ++q) {
+    const float4 v = __ldg(a4 + q), w = s4[q];
+    const float4 u = make_float4(v.x * w.x, v.y * w.y, v.z * w.z, v.w * w.w);
+    acc = fmaf(u.x, u.x, fmaf(u.y, u.y, fmaf(u.z, u.z, fmaf(u.w, u.w, acc))));
+    o4[q] = u;
+  }
+  const float inv = acc > 0.f ? 1.0f / sqrtf(acc) : 0.f;
+  for (int q = 0; q < (Fp >> 2); ++q) {
+    const float4 u = o4[q];
+    o4[q] = make_float4(u.x * inv, u.y * inv, u.z * inv, u.w * inv);
+  }
+}
+
 // A shared-memory-resident pair on a group.  Region layout (bytes):
 //   [ (1-alpha) Ehat | Y0 | Y1 ]  3 x n_row*ld floats,
 //   [ ra ]  int4 per row: first two out-neighbours {u ld 4, w}, padded; the
@@ -505,9 +524,13 @@ __device__ __forceinline__ void store_x(const Grp& grp, const Ctx& cx, const Geo
 //   [ rr ]  int4 per row: its full out- and in-edge ranges into redge,
 //   [ redge ] {u ld 4, w}: the row graph's out-edges, then in-edges,
 //   [ cedge ] {v 4, w}: the column graph's out-edges, then in-edges,
-//   [ cptr ]  the column graph's out- then in-row pointers into cedge.
-// After the iterations the Ehat buffer holds the row matching state and the
-// free iterate the column state (int16).
+//   [ cptr ]  the column graph's out- then in-row pointers into cedge,
+//   [ busy ]  the number of rows with > 2 out- or in-neighbours, then for each
+//             such row its index and its index mod R (int16).
+// Before X_0 exists, Y0 and Y1 hold the unit attribute vectors of the rows
+// and columns (stride sF floats) when they fit.  After the iterations the
+// Ehat buffer holds the row matching state and the free iterate the column
+// state (int16).
 __device__ __forceinline__ void run_pair_s(const Ctx& cx, const Geo& g, const Group& grp, unsigned char* region) {
   const Shape& s = g.s;
   const int t = grp.rank;
@@ -528,6 +551,8 @@ __device__ __forceinline__ void run_pair_s(const Ctx& cx, const Geo& g, const Gr
   const int e_col = __ldg(g.c_optr + s.n_col) - co0;
   int2* cedge = redge + 2 * e_row;
   int* cptr = reinterpret_cast<int*>(cedge + 2 * e_col);
+  int* nbusy = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(cptr) + align_up(8 * (size_t)(s.n_col + 1), 16));
+  int16_t* brow = reinterpret_cast<int16_t*>(nbusy + 2);  // [n_busy][2]: row, row mod R
   for (int k = t; k < e_col; k += grp.size) {
     const CfAdj a = ldg_adj(g.c_oadj + co0 + k), b = ldg_adj(g.c_iadj + ci0 + k);
     cedge[k] = make_int2(4 * a.nbr, __float_as_int(a.w));
@@ -553,28 +578,75 @@ __device__ __forceinline__ void run_pair_s(const Ctx& cx, const Geo& g, const Gr
     redge[k] = make_int2(4 * ld * a.nbr, __float_as_int(a.w));
     redge[e_row + k] = make_int2(4 * ld * b.nbr, __float_as_int(b.w));
   }
-  // a2: weighted attribute norms of the row blocks (buf1 is free until k = 0)
-  for (int i = t; i < s.n_row; i += grp.size) buf1[i] = attr_norm(g.r_attr + (size_t)i * cx.Fp, cx.om, cx.Fp);
+  // a2: unit attribute vectors of rows and columns in Y0/Y1 (free until X_0
+  // is written), stride sF (an odd multiple of 4 floats: conflict-free float4
+  // reads across lanes); pairs too small to hold them read the pack instead
+  const int sF = cx.Fp | 4;
+  const bool staged = 4 * (size_t)sF * (s.n_row + s.n_col) + 12 <= 8 * (size_t)nn;
+  float* ahat = reinterpret_cast<float*>(align_up(reinterpret_cast<size_t>(buf0), 16));
+  float* bhat = ahat + (size_t)s.n_row * sF;
+  if (staged) {
+    for (int k = t; k < s.n_row + s.n_col; k += grp.size) {
+      if (k < s.n_row)
+        unit_attr(g.r_attr + (size_t)k * cx.Fp, cx.sqom, cx.Fp, ahat + (size_t)k * sF);
+      else
+        unit_attr(g.c_attr + (size_t)(k - s.n_row) * cx.Fp, cx.sqom, cx.Fp, bhat + (size_t)(k - s.n_row) * sF);
+    }
+  } else {
+    for (int i = t; i < s.n_row; i += grp.size) buf1[i] = attr_norm(g.r_attr + (size_t)i * cx.Fp, cx.om, cx.Fp);
+  }
   const bool act = t < s.R * s.n_col;
   const int j = act ? t % s.n_col : 0;
   const int r0 = act ? t / s.n_col : 0;
   const int Mt = (act && s.n_row > r0) ? ceil_div(s.n_row - r0, s.R) : 0;
   const int step = s.R * ld;
   const int off0 = r0 * ld + j;
-  const float* bcol = g.c_attr + (size_t)j * cx.Fp;
-  const float cj = attr_norm(bcol, cx.om, cx.Fp);
-  grp.sync();
+  grp.sync();  // staged lists and attribute vectors visible
+
+  // the rows with further neighbours, in index order (warp 0 of the group)
+  if (grp.warp() == 0) {
+    const int lane = t & 31;
+    int cnt = 0;
+    for (int b = 0; b < s.n_row; b += 32) {
+      const int i = b + lane;
+      const bool x = i < s.n_row && ra[i].w < 0;
+      const unsigned msk = __ballot_sync(0xffffffffu, x);
+      if (x) {
+        const int q = cnt + __popc(msk & ((1u << lane) - 1u));
+        brow[2 * q] = (int16_t)i;
+        brow[2 * q + 1] = (int16_t)(i % s.R);
+      }
+      cnt += __popc(msk);
+    }
+    if (lane == 0) *nbusy = cnt;
+  }
 
   // a3: cosine attribute term E, its Frobenius norm, Ehat = X_0
   float ss = 0.f;
-  for (int m = 0, i = r0, off = off0; m < Mt; ++m, i += s.R, off += step) {
-    const float dot = attr_dot(g.r_attr + (size_t)i * cx.Fp, bcol, cx.om, cx.Fp);
-    const float den = buf1[i] * cj;
-    const float e = den > 0.f ? dot / den : 0.f;
-    ehb[off] = e;
-    ss = fmaf(e, e, ss);
+  if (staged) {
+    const float4* bj = reinterpret_cast<const float4*>(bhat + (size_t)j * sF);
+    for (int m = 0, i = r0, off = off0; m < Mt; ++m, i += s.R, off += step) {
+      const float4* ai = reinterpret_cast<const float4*>(ahat + (size_t)i * sF);
+      float e = 0.f;
+      for (int q = 0; q < (cx.Fp >> 2); ++q) {
+        const float4 u = ai[q], v = bj[q];
+        e = fmaf(u.x, v.x, fmaf(u.y, v.y, fmaf(u.z, v.z, fmaf(u.w, v.w, e))));
+      }
+      ehb[off] = e;
+      ss = fmaf(e, e, ss);
+    }
+  } else {
+    const float* bc = g.c_attr + (size_t)j * cx.Fp;
+    const float cj = attr_norm(bc, cx.om, cx.Fp);
+    for (int m = 0, i = r0, off = off0; m < Mt; ++m, i += s.R, off += step) {
+      const float dot = attr_dot(g.r_attr + (size_t)i * cx.Fp, bc, cx.om, cx.Fp);
+      const float den = buf1[i] * cj;
+      const float e = den > 0.f ? dot / den : 0.f;
+      ehb[off] = e;
+      ss = fmaf(e, e, ss);
+    }
   }
-  const float tot = grp.sum(ss, 0);
+  const float tot = grp.sum(ss, 0);  // also: every read of the attribute vectors is done
   const float inv = tot > 0.f ? 1.0f / sqrtf(tot) : 0.f;
   const float uni = 1.0f / sqrtf((float)s.n_row * (float)s.n_col);
   const float cb = 1.f - cx.alpha;
@@ -586,7 +658,12 @@ __device__ __forceinline__ void run_pair_s(const Ctx& cx, const Geo& g, const Gr
   grp.sync();  // staged column pointers visible
   const ColPad cl = load_col(cptr, cedge, s.n_col, j);
 
-  // a4: K renormalised iterations, one barrier each
+  // a4: K renormalised iterations, one barrier each.  The main sweep is the
+  // straight-line 2 x 2 gather for every entry; then the further-neighbour
+  // terms are added to the entries of busy rows (by each entry's owner) and
+  // of busy columns (by the owner's whole warp), and the norm's partial sums
+  // are updated by y_new^2 - y_old^2.
+  const int nbr = *nbusy;
   float sk = 1.f;
   for (int k = 0; k < cx.K; ++k) {
     const char* cur = reinterpret_cast<const char*>((k & 1) ? buf1 : buf0);
@@ -596,15 +673,33 @@ __device__ __forceinline__ void run_pair_s(const Ctx& cx, const Geo& g, const Gr
 #pragma unroll 2
     for (int m = 0, i = r0, off = off0; m < Mt; ++m, i += s.R, off += step) {
       const int4 A = ra[i], Q = rq[i];
-      float z = gather_fast(cur, A, Q, cl);
-      if (A.w < 0 || cl.flag) {
-        const int4 R4 = rr[i];
-        if (A.w < 0) z += row_extra(cur, R4, redge, cl);
-        if (cl.flag) z += col_extra(cur, A, Q, R4, redge, cedge, cl);
-      }
-      const float y = fmaf(ca, z, ehb[off]);
+      const float y = fmaf(ca, gather_fast(cur, A, Q, cl), ehb[off]);
       nxt[off] = y;
       ss = fmaf(y, y, ss);
+    }
+    for (int q = 0; q < nbr; ++q) {
+      if (Mt == 0 || brow[2 * q + 1] != r0) continue;  // a row of another thread
+      const int i = brow[2 * q];
+      const int off = i * ld + j;
+      const float y0 = nxt[off];
+      const float y = fmaf(ca, row_extra(cur, rr[i], redge, cl), y0);
+      nxt[off] = y;
+      ss += y * y - y0 * y0;
+    }
+    // a busy column's entries are shared out over the lanes of the warp
+    // that holds it (its owner wrote them above; __syncwarp orders that)
+    __syncwarp();
+    for (unsigned bm = __ballot_sync(0xffffffffu, cl.flag && Mt > 0); bm; bm &= bm - 1) {
+      const int bl = __ffs(bm) - 1;
+      const int jb = __shfl_sync(0xffffffffu, j, bl), ib = __shfl_sync(0xffffffffu, r0, bl);
+      const int mb = __shfl_sync(0xffffffffu, Mt, bl);
+      for (int m = t & 31; m < mb; m += 32) {
+        const int i = ib + m * s.R, off = i * ld + jb;
+        const float y0 = nxt[off];
+        const float y = fmaf(ca, col_extra(cur, ra[i], rq[i], rr[i], redge, cedge, cptr, s.n_col, jb), y0);
+        nxt[off] = y;
+        ss += y * y - y0 * y0;
+      }
     }
     const float yy = grp.sum(ss, (k + 1) & 1);
     sk = cx.norm_mode == 0 ? 1.0f / sqrtf(yy) : 1.f;
@@ -753,7 +848,7 @@ __device__ __noinline__ void run_pair_g(const Ctx& cx, const Geo& g, const Group
         if (A.w < 0 || cl.flag) {
           const int4 R4 = rr[i];
           if (A.w < 0) z += row_extra(cur, R4, redge, cl);
-          if (cl.flag) z += col_extra(cur, A, Q, R4, redge, cedge, cl);
+          if (cl.flag) z += col_extra(cur, A, Q, R4, redge, cedge, cptr, n_col, j);
         }
       } else {
         z = gather_g(reinterpret_cast<const float*>(cur), ld, g, i, j);
@@ -809,6 +904,7 @@ __device__ __forceinline__ bool make_ctx(const CallArgs& a, float* s_om, Ctx& cx
     cx.Fp = cx.A.F_pad;
     cx.ranked = a.ranked;
     cx.om = s_om;
+    cx.sqom = s_om + kMaxF;
     *s_ok = (cx.A.F == cx.B.F && cx.A.F_pad == cx.B.F_pad) ? 1 : 0;
     if (!*s_ok && blockIdx.x == 0) set_status(cx.hdr, 1 /* CF_ERR_INVALID_ARG */, -1);
   }
@@ -817,6 +913,7 @@ __device__ __forceinline__ bool make_ctx(const CallArgs& a, float* s_om, Ctx& cx
   if (threadIdx.x < kMaxF) {
     const float v = threadIdx.x < cx.F ? a.omega[threadIdx.x] : 0.f;
     s_om[threadIdx.x] = v;
+    s_om[kMaxF + threadIdx.x] = sqrtf(v);
     if (!(v >= 0.f && v <= 3.0e38f) && blockIdx.x == 0) set_status(cx.hdr, 6 /* CF_ERR_NUMERIC */, threadIdx.x);
   }
   __syncthreads();
@@ -834,7 +931,7 @@ __host__ __device__ constexpr ClassCfg fwd_cfg(int min_cls = kClassWarp, int ran
 template <int NT>
 __global__ void __launch_bounds__(NT, 1) fwd_batched_kernel(CallArgs a, int per_pair) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ __align__(16) float s_om[kMaxF];
+  __shared__ __align__(16) float s_om[2 * kMaxF];  // omega, then sqrt(omega)
   __shared__ Ctx s_cx;
   __shared__ int s_ok;
   __shared__ uint32_t s_p[1 + 4 + NT / 32];  // queue positions: CTA, quarter groups, warps
@@ -1112,14 +1209,14 @@ __device__ __noinline__ void run_pair_c(const Ctx& cx, const Geo& g, const Group
         if (A.w < 0 || cl.flag) {
           const int4 R4 = rr[lr];
           if (A.w < 0) z += row_extra(lcur, R4, redge, cl);
-          if (cl.flag) z += col_extra(lcur, A, Q, R4, redge, cedge, cl);
+          if (cl.flag) z += col_extra(lcur, A, Q, R4, redge, cedge, cptr, s.n_col, j);
         }
       } else {
         z = gather_fast(cur, A, Q, cl);
         if (A.w < 0 || cl.flag) {
           const int4 R4 = rr[lr];
           if (A.w < 0) z += row_extra(cur, R4, redge, cl);
-          if (cl.flag) z += col_extra(cur, A, Q, R4, redge, cedge, cl);
+          if (cl.flag) z += col_extra(cur, A, Q, R4, redge, cedge, cptr, s.n_col, j);
         }
       }
       const float y = fmaf(ca, z, ehb[off]);
@@ -1159,7 +1256,7 @@ __device__ __noinline__ void run_pair_c(const Ctx& cx, const Geo& g, const Group
 template <int NT>
 __global__ void __launch_bounds__(NT, 1) fwd_cluster_kernel(CallArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ __align__(16) float s_om[kMaxF];
+  __shared__ __align__(16) float s_om[2 * kMaxF];  // omega, then sqrt(omega)
   __shared__ Ctx s_cx;
   __shared__ int s_ok;
   __shared__ ClState st;

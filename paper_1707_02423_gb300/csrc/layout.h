@@ -94,10 +94,11 @@ CF_HD int pair_ld(int n_col) { return n_col | 1; }  // odd stride: column scans 
 // in-neighbours padded to two (two int4) and its full edge ranges (int4);
 // the row graph's out- then in-edge entries and the column graph's out- then
 // in-edge entries ({byte offset, w}, 8 bytes each); the column graph's out-
-// and in-edge row pointers (int32, n_col + 1 each).
+// and in-edge row pointers (int32, n_col + 1 each); the list of rows with
+// more than two out- or in-neighbours (a count, then int16 pairs).
 CF_HD size_t resident_bytes(int n_row, int ld, int e_row, int n_col, int e_col) {
   return align_up(12 * (size_t)n_row * ld, 16) + 48 * (size_t)n_row + 16 * (size_t)e_row + 16 * (size_t)e_col +
-         align_up(8 * (size_t)(n_col + 1), 16);
+         align_up(8 * (size_t)(n_col + 1), 16) + align_up(8 + 4 * (size_t)n_row, 16);
 }
 
 CF_HD bool fits(int n_row, int n_col, int e_row, int e_col, int G, size_t region, int* R, int* M) {
