@@ -296,9 +296,10 @@ cf_status cf_similarity_noalloc(const void* d_pack_a, const void* d_pack_b, cons
 /* ---- a7: autotuner --------------------------------------------------------- */
 /* Kernel configurations of the batched forward, by tune id (cf_params.tune):
  * threads per CTA (1024 or 512), the smallest thread group a pair may be
- * given (a warp, a quarter CTA, or the whole CTA), the matching policy of
- * shared-memory-resident pairs (ranked lists wherever their state fits, only
- * below the whole-CTA level, or never: rounds of rescans), and the cluster
+ * given (a warp, a quarter CTA, a half CTA or the whole CTA), the matching
+ * policy of shared-memory-resident pairs (ranked lists wherever their state
+ * fits, only in groups of at most a quarter CTA, or never: rounds of
+ * rescans), and the cluster
  * tier: pairs too large for one CTA split by rows over the 2, 4 or 8 CTAs of
  * a thread-block cluster with the iterates in distributed shared memory (or,
  * with no cluster tier, iterated by one CTA out of L2).  Every tune gives the
@@ -306,9 +307,10 @@ cf_status cf_similarity_noalloc(const void* d_pack_a, const void* d_pack_b, cons
 typedef struct cf_tune_info {
   int32_t tune;
   int32_t threads_per_cta; /* 1024 or 512                                     */
-  int32_t smallest_group;  /* threads: 32, threads_per_cta / 4 or threads_per_cta */
-  int32_t matching;        /* 0 ranked where it fits, 1 ranked below the whole
-                              CTA, 2 rescans only                               */
+  int32_t smallest_group;  /* threads: 32, threads_per_cta / 4, threads_per_cta / 2
+                              or threads_per_cta                                */
+  int32_t matching;        /* 0 ranked where it fits, 1 ranked in groups of at
+                              most a quarter CTA, 2 rescans only                */
   int32_t cluster;         /* CTAs per thread-block cluster of the cluster tier
                               (0: none; pairs too large for one CTA then use the
                               global-memory tier)                               */

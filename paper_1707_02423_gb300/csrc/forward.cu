@@ -1,15 +1,18 @@
 // a2-a7: the batched similarity forward, greedy matching and graph score.
 //
-// One persistent kernel, one 1024-thread CTA per SM, drains four cost-ordered
+// One persistent kernel, one 1024-thread CTA per SM, drains five cost-ordered
 // queues (filled by plan.cu), largest work first:
 //   global class:  pairs too large for shared memory; the whole CTA iterates X
 //                  in a scratch slot of the workspace (L2-resident),
 //   CTA class:     the whole CTA keeps the pair in its 220 KB of shared memory,
+//   half class:    two 512-thread groups (named barriers 5-6) each keep a pair
+//                  in their half of the shared memory,
 //   quarter class: four 256-thread groups (named barriers 1-4) each keep a
 //                  pair in their quarter of the shared memory,
 //   warp class:    every warp keeps a small pair in its own 1/32 slice.
-// A quarter group that finds its queue empty goes straight on to warp-class
-// pairs in its own slices, so the tail of one class overlaps the next.
+// A group that finds its queue empty goes straight on to the next level's
+// pairs in its own part of the shared memory, so the tail of one class
+// overlaps the next.
 //
 // Iteration (Table 1 "Iso" row, IsoRank-style, renormalised every step):
 //   Y_{k+1} = alpha/2 (W_A X_k W_B^T + W_A^T X_k W_B) + (1 - alpha) Ehat,
@@ -713,7 +716,7 @@ __device__ __forceinline__ void run_pair_s(const Ctx& cx, const Geo& g, const Gr
   if (cx.X) store_x(grp, cx, g, Xs, ld);
   if (cx.scores || cx.match) {
     int32_t* mo = cx.match ? cx.match + cx.m_off[g.p] : nullptr;
-    const bool ranked = cx.ranked == 0 || (cx.ranked == 1 && grp.bar != 0);  // bar 0: the whole CTA
+    const bool ranked = cx.ranked == 0 || (cx.ranked == 1 && 4 * grp.size <= (int)blockDim.x);
     if (ranked && 5 * (size_t)(s.n_row + s.n_col) + 16 <= 4 * (size_t)nn) {  // room for the ranked lists' state
       const float sc = greedy_ranked(grp, Xs, ld, s.n_row, s.n_col, s.tr, reinterpret_cast<int16_t*>(ehb),
                                      reinterpret_cast<int16_t*>(ehb) + s.n_row * s.n_col,
@@ -921,11 +924,13 @@ __device__ __forceinline__ bool make_ctx(const CallArgs& a, float* s_om, Ctx& cx
 }
 
 // The persistent kernel's shapes: NT threads, one CTA per SM, 220 KB of
-// dynamic shared memory split 1 / 4 / (NT/32) ways for the three group levels.
+// dynamic shared memory split 1 / 2 / 4 / (NT/32) ways for the four group
+// levels.
 constexpr size_t kFwdSmem = 225280;
 template <int NT>
 __host__ __device__ constexpr ClassCfg fwd_cfg(int min_cls = kClassWarp, int ranked = 0, int cluster = 0) {
-  return ClassCfg{NT, (int)kFwdSmem, (int)kFwdSmem / 4, (int)kFwdSmem / (NT / 32), min_cls, ranked, cluster};
+  return ClassCfg{NT,      (int)kFwdSmem, (int)kFwdSmem / 2, (int)kFwdSmem / 4, (int)kFwdSmem / (NT / 32),
+                  min_cls, ranked,         cluster};
 }
 
 template <int NT>
@@ -934,9 +939,9 @@ __global__ void __launch_bounds__(NT, 1) fwd_batched_kernel(CallArgs a, int per_
   __shared__ __align__(16) float s_om[2 * kMaxF];  // omega, then sqrt(omega)
   __shared__ Ctx s_cx;
   __shared__ int s_ok;
-  __shared__ uint32_t s_p[1 + 4 + NT / 32];  // queue positions: CTA, quarter groups, warps
-  __shared__ float s_redf[5][64];       // partials of the CTA group and the four quarter groups
-  __shared__ int s_redi[5][64];
+  __shared__ uint32_t s_p[1 + 2 + 4 + NT / 32];  // queue positions: CTA, half and quarter groups, warps
+  __shared__ float s_redf[7][64];  // partials of the CTA group, the two half and the four quarter groups
+  __shared__ int s_redi[7][64];
   if (!make_ctx(a, s_om, s_cx, &s_ok)) return;
   const Ctx& cx = s_cx;
   const bool single = per_pair >= 0;  // the plain form: one launch runs exactly one pair on the whole CTA
@@ -973,23 +978,29 @@ __global__ void __launch_bounds__(NT, 1) fwd_batched_kernel(CallArgs a, int per_
     }
   }
   // shared-memory classes, one level after the other: the whole CTA, then
-  // four quarter groups (named barriers 1..4), then single warps.  Each level
-  // is a sub-partition of the previous one's region, and every group ends a
-  // pair with its own barrier, so no CTA-wide barrier sits between levels.
+  // two half groups (named barriers 5..6), four quarter groups (named
+  // barriers 1..4), then single warps.  Each level is a sub-partition of the
+  // previous one's region, and every group ends a pair with its own barrier,
+  // so no CTA-wide barrier sits between levels.
   uint32_t qbase = n[kClassGlobal];
   for (int level = kClassCta; level <= cc.min_cls; ++level) {
     Group grp = cta;
     unsigned char* region = smem;
     int slot = 0;
-    if (level == kClassQuarter) {
+    if (level == kClassHalf) {
+      const int hg = t / (NT / 2);
+      grp = Group{t % (NT / 2), NT / 2, 5 + hg, s_redf[1 + hg], s_redi[1 + hg]};
+      region = smem + (size_t)hg * cc.z_half;
+      slot = 1 + hg;
+    } else if (level == kClassQuarter) {
       const int qg = t / (NT / 4);
-      grp = Group{t % (NT / 4), NT / 4, 1 + qg, s_redf[1 + qg], s_redi[1 + qg]};
+      grp = Group{t % (NT / 4), NT / 4, 1 + qg, s_redf[3 + qg], s_redi[3 + qg]};
       region = smem + (size_t)qg * cc.z_qtr;
-      slot = 1 + qg;
+      slot = 3 + qg;
     } else if (level == kClassWarp) {
       grp = Group{t & 31, 32, -1, nullptr, nullptr};
       region = smem + (size_t)(t >> 5) * cc.z_wrp;
-      slot = 5 + (t >> 5);
+      slot = 7 + (t >> 5);
     }
     const uint32_t count = single ? 1u : n[level];
     for (;;) {

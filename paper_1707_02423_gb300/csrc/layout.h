@@ -50,17 +50,18 @@ struct PackHeader {
 };
 
 // Execution classes of a pair, in queue order: the global-memory tier, the
-// three shared-memory group levels of the persistent kernel (whole CTA,
-// quarter CTA, single warp), and the cluster tier (rows split over the CTAs
-// of a thread-block cluster, iterate in distributed shared memory).
+// four shared-memory group levels of the persistent kernel (whole CTA, half
+// CTA, quarter CTA, single warp), and the cluster tier (rows split over the
+// CTAs of a thread-block cluster, iterate in distributed shared memory).
 enum PairClass : int {
   kClassGlobal = 0,
   kClassCta = 1,
-  kClassQuarter = 2,
-  kClassWarp = 3,
-  kClassCluster = 4,
-  kNumClasses = 5,
-  kClassSkip = 5
+  kClassHalf = 2,
+  kClassQuarter = 3,
+  kClassWarp = 4,
+  kClassCluster = 5,
+  kNumClasses = 6,
+  kClassSkip = 6
 };
 constexpr int kMaxCluster = 16;
 constexpr int kBuckets = 64;  // cost buckets per class (two per octave)
@@ -71,11 +72,13 @@ constexpr int kBuckets = 64;  // cost buckets per class (two per octave)
 struct ClassCfg {
   int nt;       // threads per CTA (the CTA-level group)
   int z_cta;    // region of the CTA-level group
+  int z_half;   // region of each of the two half groups (nt / 2 threads)
   int z_qtr;    // region of each of the four quarter groups (nt / 4 threads)
   int z_wrp;    // region of each warp
   int min_cls;  // smallest group level pairs may go to (kClassWarp: all levels)
   int ranked;   // matching of resident pairs: 0 ranked lists wherever their
-                // state fits, 1 only below the whole-CTA level, 2 never (rescans)
+                // state fits, 1 only in groups of at most a quarter CTA,
+                // 2 never (rescans)
   int cluster;  // CTAs per cluster of the cluster tier (0: no cluster tier)
 };
 
@@ -109,11 +112,14 @@ CF_HD bool fits(int n_row, int n_col, int e_row, int e_col, int G, size_t region
 }
 
 CF_HD int group_size(int cls, const ClassCfg& c) {
-  return cls == kClassWarp ? 32 : cls == kClassQuarter ? c.nt / 4 : c.nt;
+  return cls == kClassWarp ? 32 : cls == kClassQuarter ? c.nt / 4 : cls == kClassHalf ? c.nt / 2 : c.nt;
 }
 
 CF_HD size_t group_region(int cls, const ClassCfg& c) {
-  return (size_t)(cls == kClassWarp ? c.z_wrp : cls == kClassQuarter ? c.z_qtr : c.z_cta);
+  return (size_t)(cls == kClassWarp      ? c.z_wrp
+                  : cls == kClassQuarter ? c.z_qtr
+                  : cls == kClassHalf    ? c.z_half
+                                         : c.z_cta);
 }
 
 // Orientation of a pair that fits both ways: the column graph's lists live in
