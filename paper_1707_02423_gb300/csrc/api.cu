@@ -303,9 +303,9 @@ Tune decode_tune(int32_t id) {
   const int idx = id >= 1 && id <= kNumTunes ? id - 1 : 0;
   Tune t;
   t.variant = idx % 2;
-  t.min_cls = kClassWarp - (idx / 2) % 4;
-  t.ranked = (idx / 8) % 3;
-  t.cluster = kClusters[idx / 24];
+  t.min_cls = kClassWarp - (idx / 2) % 5;
+  t.ranked = (idx / 10) % 3;
+  t.cluster = kClusters[idx / 30];
   return t;
 }
 }  // namespace cfsim

@@ -1,6 +1,6 @@
 // a2-a7: the batched similarity forward, greedy matching and graph score.
 //
-// One persistent kernel, one 1024-thread CTA per SM, drains five cost-ordered
+// One persistent kernel, one 1024-thread CTA per SM, drains six cost-ordered
 // queues (filled by plan.cu), largest work first:
 //   global class:  pairs too large for shared memory; the whole CTA iterates X
 //                  in a scratch slot of the workspace (L2-resident),
@@ -9,6 +9,8 @@
 //                  in their half of the shared memory,
 //   quarter class: four 256-thread groups (named barriers 1-4) each keep a
 //                  pair in their quarter of the shared memory,
+//   eighth class:  eight 128-thread groups (named barriers 7-14) each keep a
+//                  pair in their eighth of the shared memory,
 //   warp class:    every warp keeps a small pair in its own 1/32 slice.
 // A group that finds its queue empty goes straight on to the next level's
 // pairs in its own part of the shared memory, so the tail of one class
@@ -100,7 +102,7 @@ __device__ __forceinline__ Geo make_geo(const Ctx& cx, int p, const ClassCfg& cc
 // A group of threads working on one pair: a single warp (bar < 0) or a set of
 // whole warps synchronised by named barrier `bar`.  sum() contains the
 // group's one barrier; `redf`/`redi` hold two parities of per-warp partials
-// so that consecutive sums need no second barrier.
+// (2 * size / 32 entries) so that consecutive sums need no second barrier.
 struct Group {
   int rank, size, bar;
   float* redf;
@@ -123,9 +125,9 @@ struct Group {
       return v;
     }
     const int lane = rank & 31;
-    if (lane == 0) redf[par * 32 + (rank >> 5)] = v;
+    if (lane == 0) redf[par * (size >> 5) + (rank >> 5)] = v;
     bar_sync(bar, size);
-    return warp_sum(lane < (size >> 5) ? redf[par * 32 + lane] : 0.f);
+    return warp_sum(lane < (size >> 5) ? redf[par * (size >> 5) + lane] : 0.f);
   }
   __device__ __forceinline__ int sum_i(int v, int par) const {
     v = warp_sum_i(v);
@@ -134,9 +136,9 @@ struct Group {
       return v;
     }
     const int lane = rank & 31;
-    if (lane == 0) redi[par * 32 + (rank >> 5)] = v;
+    if (lane == 0) redi[par * (size >> 5) + (rank >> 5)] = v;
     bar_sync(bar, size);
-    return warp_sum_i(lane < (size >> 5) ? redi[par * 32 + lane] : 0);
+    return warp_sum_i(lane < (size >> 5) ? redi[par * (size >> 5) + lane] : 0);
   }
 };
 
@@ -924,13 +926,20 @@ __device__ __forceinline__ bool make_ctx(const CallArgs& a, float* s_om, Ctx& cx
 }
 
 // The persistent kernel's shapes: NT threads, one CTA per SM, 220 KB of
-// dynamic shared memory split 1 / 2 / 4 / (NT/32) ways for the four group
+// dynamic shared memory split 1 / 2 / 4 / 8 / (NT/32) ways for the five group
 // levels.
 constexpr size_t kFwdSmem = 225280;
 template <int NT>
 __host__ __device__ constexpr ClassCfg fwd_cfg(int min_cls = kClassWarp, int ranked = 0, int cluster = 0) {
-  return ClassCfg{NT,      (int)kFwdSmem, (int)kFwdSmem / 2, (int)kFwdSmem / 4, (int)kFwdSmem / (NT / 32),
-                  min_cls, ranked,         cluster};
+  return ClassCfg{NT,
+                  (int)kFwdSmem,
+                  (int)kFwdSmem / 2,
+                  (int)kFwdSmem / 4,
+                  (int)kFwdSmem / 8,
+                  (int)kFwdSmem / (NT / 32),
+                  min_cls,
+                  ranked,
+                  cluster};
 }
 
 template <int NT>
@@ -939,9 +948,11 @@ __global__ void __launch_bounds__(NT, 1) fwd_batched_kernel(CallArgs a, int per_
   __shared__ __align__(16) float s_om[2 * kMaxF];  // omega, then sqrt(omega)
   __shared__ Ctx s_cx;
   __shared__ int s_ok;
-  __shared__ uint32_t s_p[1 + 2 + 4 + NT / 32];  // queue positions: CTA, half and quarter groups, warps
-  __shared__ float s_redf[7][64];  // partials of the CTA group, the two half and the four quarter groups
-  __shared__ int s_redi[7][64];
+  __shared__ uint32_t s_p[1 + 2 + 4 + 8 + NT / 32];  // queue positions: CTA, half, quarter, eighth groups, warps
+  // per-warp partials, two parities, of the CTA group, then the half,
+  // quarter and eighth groups: 2 * NT / 32 entries per level
+  __shared__ float s_redf[4][2 * NT / 32];
+  __shared__ int s_redi[4][2 * NT / 32];
   if (!make_ctx(a, s_om, s_cx, &s_ok)) return;
   const Ctx& cx = s_cx;
   const bool single = per_pair >= 0;  // the plain form: one launch runs exactly one pair on the whole CTA
@@ -979,7 +990,8 @@ __global__ void __launch_bounds__(NT, 1) fwd_batched_kernel(CallArgs a, int per_
   }
   // shared-memory classes, one level after the other: the whole CTA, then
   // two half groups (named barriers 5..6), four quarter groups (named
-  // barriers 1..4), then single warps.  Each level is a sub-partition of the
+  // barriers 1..4), eight eighth groups (named barriers 7..14), then single
+  // warps.  Each level is a sub-partition of the
   // previous one's region, and every group ends a pair with its own barrier,
   // so no CTA-wide barrier sits between levels.
   uint32_t qbase = n[kClassGlobal];
@@ -989,18 +1001,23 @@ __global__ void __launch_bounds__(NT, 1) fwd_batched_kernel(CallArgs a, int per_
     int slot = 0;
     if (level == kClassHalf) {
       const int hg = t / (NT / 2);
-      grp = Group{t % (NT / 2), NT / 2, 5 + hg, s_redf[1 + hg], s_redi[1 + hg]};
+      grp = Group{t % (NT / 2), NT / 2, 5 + hg, s_redf[1] + hg * (NT / 32), s_redi[1] + hg * (NT / 32)};
       region = smem + (size_t)hg * cc.z_half;
       slot = 1 + hg;
     } else if (level == kClassQuarter) {
       const int qg = t / (NT / 4);
-      grp = Group{t % (NT / 4), NT / 4, 1 + qg, s_redf[3 + qg], s_redi[3 + qg]};
+      grp = Group{t % (NT / 4), NT / 4, 1 + qg, s_redf[2] + qg * (NT / 64), s_redi[2] + qg * (NT / 64)};
       region = smem + (size_t)qg * cc.z_qtr;
       slot = 3 + qg;
+    } else if (level == kClassEighth) {
+      const int eg = t / (NT / 8);
+      grp = Group{t % (NT / 8), NT / 8, 7 + eg, s_redf[3] + eg * (NT / 128), s_redi[3] + eg * (NT / 128)};
+      region = smem + (size_t)eg * cc.z_8th;
+      slot = 7 + eg;
     } else if (level == kClassWarp) {
       grp = Group{t & 31, 32, -1, nullptr, nullptr};
       region = smem + (size_t)(t >> 5) * cc.z_wrp;
-      slot = 7 + (t >> 5);
+      slot = 15 + (t >> 5);
     }
     const uint32_t count = single ? 1u : n[level];
     for (;;) {

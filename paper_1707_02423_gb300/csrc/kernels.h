@@ -46,7 +46,7 @@ ClassCfg fwd_class_cfg(int v, int min_cls, int ranked, int cluster);
 int cluster_supported(int v, int C);
 
 // Kernel configuration selected by cf_params.tune (see decode_tune).
-constexpr int kNumTunes = 96;
+constexpr int kNumTunes = 120;
 struct Tune {
   int variant, min_cls, ranked, cluster;
 };

@@ -50,18 +50,19 @@ struct PackHeader {
 };
 
 // Execution classes of a pair, in queue order: the global-memory tier, the
-// four shared-memory group levels of the persistent kernel (whole CTA, half
-// CTA, quarter CTA, single warp), and the cluster tier (rows split over the
-// CTAs of a thread-block cluster, iterate in distributed shared memory).
+// five shared-memory group levels of the persistent kernel (whole CTA, half,
+// quarter and eighth CTA, single warp), and the cluster tier (rows split over
+// the CTAs of a thread-block cluster, iterate in distributed shared memory).
 enum PairClass : int {
   kClassGlobal = 0,
   kClassCta = 1,
   kClassHalf = 2,
   kClassQuarter = 3,
-  kClassWarp = 4,
-  kClassCluster = 5,
-  kNumClasses = 6,
-  kClassSkip = 6
+  kClassEighth = 4,
+  kClassWarp = 5,
+  kClassCluster = 6,
+  kNumClasses = 7,
+  kClassSkip = 7
 };
 constexpr int kMaxCluster = 16;
 constexpr int kBuckets = 64;  // cost buckets per class (two per octave)
@@ -74,6 +75,7 @@ struct ClassCfg {
   int z_cta;    // region of the CTA-level group
   int z_half;   // region of each of the two half groups (nt / 2 threads)
   int z_qtr;    // region of each of the four quarter groups (nt / 4 threads)
+  int z_8th;    // region of each of the eight eighth groups (nt / 8 threads)
   int z_wrp;    // region of each warp
   int min_cls;  // smallest group level pairs may go to (kClassWarp: all levels)
   int ranked;   // matching of resident pairs: 0 ranked lists wherever their
@@ -112,11 +114,16 @@ CF_HD bool fits(int n_row, int n_col, int e_row, int e_col, int G, size_t region
 }
 
 CF_HD int group_size(int cls, const ClassCfg& c) {
-  return cls == kClassWarp ? 32 : cls == kClassQuarter ? c.nt / 4 : cls == kClassHalf ? c.nt / 2 : c.nt;
+  return cls == kClassWarp      ? 32
+         : cls == kClassEighth  ? c.nt / 8
+         : cls == kClassQuarter ? c.nt / 4
+         : cls == kClassHalf    ? c.nt / 2
+                                : c.nt;
 }
 
 CF_HD size_t group_region(int cls, const ClassCfg& c) {
   return (size_t)(cls == kClassWarp      ? c.z_wrp
+                  : cls == kClassEighth  ? c.z_8th
                   : cls == kClassQuarter ? c.z_qtr
                   : cls == kClassHalf    ? c.z_half
                                          : c.z_cta);

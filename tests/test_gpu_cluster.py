@@ -19,7 +19,7 @@ DEV = "cuda:0"
 def tune_id(variant, cluster_index, min_level=0, ranked=0):
     """Tune id of (threads variant, smallest-group level, matching policy,
     cluster size index into (0, 2, 4, 8))."""
-    return 1 + variant + 2 * min_level + 8 * ranked + 24 * cluster_index
+    return 1 + variant + 2 * min_level + 10 * ranked + 30 * cluster_index
 
 
 @pytest.fixture(scope="module")

@@ -34,7 +34,7 @@ def wl():
     return w, pa, torch.tensor(om, dtype=torch.float32, device=DEV), ref
 
 
-NT = 96
+NT = 120
 
 
 def test_tune_table():
@@ -44,7 +44,7 @@ def test_tune_table():
     for t in range(0, NT + 1):
         d = api.tune_info(t)
         assert d["threads_per_cta"] in (512, 1024)
-        assert d["smallest_group"] in (32, d["threads_per_cta"] // 4, d["threads_per_cta"] // 2, d["threads_per_cta"])
+        assert d["smallest_group"] in (32, *(d["threads_per_cta"] // k for k in (8, 4, 2, 1)))
         assert d["cluster"] in (0, 2, 4, 8)
         if t > 0:
             seen.add((d["threads_per_cta"], d["smallest_group"], d["matching"], d["cluster"]))
@@ -52,7 +52,7 @@ def test_tune_table():
     assert api.tune_info(0) == {**api.tune_info(1), "tune": 0}
 
 
-@pytest.mark.parametrize("tune", list(range(1, NT + 1, 5)) + [3, 5, 7, 24, 25, 48, 49, 72, 73, 96])
+@pytest.mark.parametrize("tune", list(range(1, NT + 1, 5)) + [3, 5, 7, 9, 30, 31, 60, 61, 90, 91, 120])
 def test_every_tune_matches_oracle(wl, tune):
     w, pa, om, ref = wl
     res = api.similarity(pa, pa, w.pairs, om, 0.8, 40, want_match=True, tune=tune)
