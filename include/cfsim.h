@@ -295,7 +295,7 @@ cf_status cf_similarity_noalloc(const void* d_pack_a, const void* d_pack_b, cons
 
 /* ---- a7: autotuner --------------------------------------------------------- */
 /* Kernel configurations of the batched forward, by tune id (cf_params.tune):
- * threads per CTA (1024 or 512), the smallest thread group a pair may be
+ * threads per CTA (1024, 768 or 512), the smallest thread group a pair may be
  * given (a warp, an eighth, quarter or half CTA, or the whole CTA), the matching
  * policy of shared-memory-resident pairs (ranked lists wherever their state
  * fits, only in groups of at most a quarter CTA, or never: rounds of
@@ -306,7 +306,7 @@ cf_status cf_similarity_noalloc(const void* d_pack_a, const void* d_pack_b, cons
  * same results up to rounding; only the speed differs. */
 typedef struct cf_tune_info {
   int32_t tune;
-  int32_t threads_per_cta; /* 1024 or 512                                     */
+  int32_t threads_per_cta; /* 1024, 768 or 512                                */
   int32_t smallest_group;  /* threads: 32, or threads_per_cta / 8, / 4, / 2, / 1 */
   int32_t matching;        /* 0 ranked where it fits, 1 ranked in groups of at
                               most a quarter CTA, 2 rescans only                */

@@ -302,10 +302,10 @@ Tune decode_tune(int32_t id) {
   static const int kClusters[4] = {0, 2, 4, 8};
   const int idx = id >= 1 && id <= kNumTunes ? id - 1 : 0;
   Tune t;
-  t.variant = idx % 2;
-  t.min_cls = kClassWarp - (idx / 2) % 5;
-  t.ranked = (idx / 10) % 3;
-  t.cluster = kClusters[idx / 30];
+  t.variant = idx % 3;
+  t.min_cls = kClassWarp - (idx / 3) % 5;
+  t.ranked = (idx / 15) % 3;
+  t.cluster = kClusters[idx / 45];
   return t;
 }
 }  // namespace cfsim

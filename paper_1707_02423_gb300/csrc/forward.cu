@@ -936,7 +936,7 @@ __host__ __device__ constexpr ClassCfg fwd_cfg(int min_cls = kClassWarp, int ran
                   (int)kFwdSmem / 2,
                   (int)kFwdSmem / 4,
                   (int)kFwdSmem / 8,
-                  (int)kFwdSmem / (NT / 32),
+                  ((int)kFwdSmem / (NT / 32)) & ~15,
                   min_cls,
                   ranked,
                   cluster};
@@ -1467,24 +1467,33 @@ cudaError_t launch_cluster(const CallArgs& a, cudaStream_t s) {
 }  // namespace
 
 int cluster_supported(int v, int C) {
-  const int n = v == 1 ? resident_clusters<512>(C) : resident_clusters<1024>(C);
+  const int n = v == 1   ? resident_clusters<512>(C)
+                : v == 2 ? resident_clusters<768>(C)
+                         : resident_clusters<1024>(C);
   return n > 0 ? C : 0;
 }
 
 // Variants of the persistent forward kernel: 0 = 1024 threads (64 registers,
-// 32 warps per SM), 1 = 512 threads (128 registers, 16 warps per SM).
-int num_fwd_variants() { return 2; }
+// 32 warps per SM), 1 = 512 threads (128 registers, 16 warps per SM), 2 = 768
+// threads (80 registers, 24 warps per SM).
+int num_fwd_variants() { return 3; }
 
 ClassCfg fwd_class_cfg(int v, int min_cls, int ranked, int cluster) {
-  return v == 1 ? fwd_cfg<512>(min_cls, ranked, cluster) : fwd_cfg<1024>(min_cls, ranked, cluster);
+  return v == 1   ? fwd_cfg<512>(min_cls, ranked, cluster)
+         : v == 2 ? fwd_cfg<768>(min_cls, ranked, cluster)
+                  : fwd_cfg<1024>(min_cls, ranked, cluster);
 }
 
 cudaError_t launch_forward(const CallArgs& a, int variant, bool per_pair, cudaStream_t s) {
   if (!per_pair && a.cluster >= 2) {  // the cluster tier first: its pairs are the largest
-    const cudaError_t e = variant == 1 ? launch_cluster<512>(a, s) : launch_cluster<1024>(a, s);
+    const cudaError_t e = variant == 1   ? launch_cluster<512>(a, s)
+                          : variant == 2 ? launch_cluster<768>(a, s)
+                                         : launch_cluster<1024>(a, s);
     if (e != cudaSuccess) return e;
   }
-  return variant == 1 ? launch_fwd<512>(a, per_pair, s) : launch_fwd<1024>(a, per_pair, s);
+  return variant == 1   ? launch_fwd<512>(a, per_pair, s)
+         : variant == 2 ? launch_fwd<768>(a, per_pair, s)
+                        : launch_fwd<1024>(a, per_pair, s);
 }
 
 cudaError_t launch_match_only(const CallArgs& a, cudaStream_t s) {

@@ -37,7 +37,7 @@ struct CallArgs {
   int cluster;  // CTAs per cluster of the cluster tier, 0 = none
 };
 
-// Batched forward kernel variants: 0 = 1024 threads per CTA, 1 = 512.
+// Batched forward kernel variants: 0 = 1024 threads per CTA, 1 = 512, 2 = 768.
 int num_fwd_variants();
 // Class configuration of variant v with the given smallest group level,
 // matching policy and cluster size.
@@ -46,7 +46,7 @@ ClassCfg fwd_class_cfg(int v, int min_cls, int ranked, int cluster);
 int cluster_supported(int v, int C);
 
 // Kernel configuration selected by cf_params.tune (see decode_tune).
-constexpr int kNumTunes = 120;
+constexpr int kNumTunes = 180;
 struct Tune {
   int variant, min_cls, ranked, cluster;
 };

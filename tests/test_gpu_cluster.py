@@ -19,7 +19,7 @@ DEV = "cuda:0"
 def tune_id(variant, cluster_index, min_level=0, ranked=0):
     """Tune id of (threads variant, smallest-group level, matching policy,
     cluster size index into (0, 2, 4, 8))."""
-    return 1 + variant + 2 * min_level + 10 * ranked + 30 * cluster_index
+    return 1 + variant + 3 * min_level + 15 * ranked + 45 * cluster_index
 
 
 @pytest.fixture(scope="module")
@@ -47,7 +47,7 @@ def wl():
     return cfgs, pairs, pa, torch.tensor(om, dtype=torch.float32, device=DEV), ref
 
 
-@pytest.mark.parametrize("variant,ci", [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3)])
+@pytest.mark.parametrize("variant,ci", [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 2)])
 def test_cluster_sizes_match_oracle(wl, variant, ci):
     cfgs, pairs, pa, om, ref = wl
     res = api.similarity(pa, pa, pairs, om, 0.8, 40, want_x=True, want_match=True, tune=tune_id(variant, ci))

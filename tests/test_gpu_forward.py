@@ -156,7 +156,7 @@ def test_query_shape_f25():
     compare(w.cfgs_a, w.cfgs_b, w.pairs, w.F)
 
 
-@pytest.mark.parametrize("tune", [0, 1 + 30 * 2, 1 + 30 * 3])  # one CTA per pair; 4- and 8-CTA cluster teams
+@pytest.mark.parametrize("tune", [0, 1 + 45 * 2, 1 + 45 * 3])  # one CTA per pair; 4- and 8-CTA cluster teams
 def test_large_cfgs_global_class(tune):
     w = config3(3, 500, 900)
     compare(w.cfgs_a, w.cfgs_a, w.pairs, w.F, tune=tune)

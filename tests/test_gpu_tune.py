@@ -34,7 +34,7 @@ def wl():
     return w, pa, torch.tensor(om, dtype=torch.float32, device=DEV), ref
 
 
-NT = 120
+NT = 180
 
 
 def test_tune_table():
@@ -43,7 +43,7 @@ def test_tune_table():
     seen = set()
     for t in range(0, NT + 1):
         d = api.tune_info(t)
-        assert d["threads_per_cta"] in (512, 1024)
+        assert d["threads_per_cta"] in (512, 768, 1024)
         assert d["smallest_group"] in (32, *(d["threads_per_cta"] // k for k in (8, 4, 2, 1)))
         assert d["cluster"] in (0, 2, 4, 8)
         if t > 0:
@@ -52,7 +52,7 @@ def test_tune_table():
     assert api.tune_info(0) == {**api.tune_info(1), "tune": 0}
 
 
-@pytest.mark.parametrize("tune", list(range(1, NT + 1, 5)) + [3, 5, 7, 9, 30, 31, 60, 61, 90, 91, 120])
+@pytest.mark.parametrize("tune", list(range(1, NT + 1, 7)) + [2, 3, 6, 9, 12, 15, 45, 46, 47, 90, 92, 135, 136, 180])
 def test_every_tune_matches_oracle(wl, tune):
     w, pa, om, ref = wl
     res = api.similarity(pa, pa, w.pairs, om, 0.8, 40, want_match=True, tune=tune)
