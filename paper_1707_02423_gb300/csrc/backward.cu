@@ -20,7 +20,7 @@
 // segments backwards, recomputing each segment's iterates from its checkpoint
 // (about 2K forward steps and K adjoint steps; S + K/S + 1 matrices resident).
 //
-// A pair runs on a team: one 256-thread CTA, or -- for the pairs too large
+// A pair runs on a team: one 1024-thread CTA, or -- for the pairs too large
 // for one CTA's shared memory in the forward, whose single-CTA adjoint would
 // be the critical path of a batch -- all CTAs of a thread-block cluster.  All
 // matrices live in a scratch slot of the workspace (L2-resident).  Element
@@ -37,7 +37,12 @@ namespace cfsim {
 
 namespace {
 
-constexpr int kBwdNT = 256;
+// A batch's adjoint time is the critical path of its largest pairs (a
+// serial chain of about 3K sweeps, each ending in a team barrier), so teams
+// are as wide as possible: 1024-thread CTAs (64 registers) beat 256- and
+// 512-thread CTAs with more registers and more CTAs per SM (256 seeded
+// pairs, n 10-300: 14.6 ms against 24.5 and 16.8 ms).
+constexpr int kBwdNT = 1024;
 constexpr int kBwdWarps = kBwdNT / 32;
 
 // The threads working on one pair: one CTA (C == 1) or the C CTAs of a
