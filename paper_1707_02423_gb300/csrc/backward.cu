@@ -433,9 +433,9 @@ __device__ __forceinline__ BwdPair bwd_pair(const BwdCtx& cx, uint32_t qi) {
   return q;
 }
 
-// One CTA per pair.  first: where in the queue this kernel starts (after the
-// pairs a cluster launch took, or 0).
-__global__ void __launch_bounds__(kBwdNT, 1) bwd_kernel(CallArgs a, uint32_t first) {
+// One CTA per pair, every pair of the queue (used when no cluster of
+// kBwdCluster CTAs fits on the device).
+__global__ void __launch_bounds__(kBwdNT, 1) bwd_kernel(CallArgs a) {
   __shared__ __align__(16) float s_om[kMaxF];
   __shared__ float s_red[64];
   __shared__ BwdCtx s_cx;
@@ -451,9 +451,8 @@ __global__ void __launch_bounds__(kBwdNT, 1) bwd_kernel(CallArgs a, uint32_t fir
   if (blockIdx.x >= nslots) return;
   float* slot = reinterpret_cast<float*>(cx.slots + (size_t)blockIdx.x * need);
   const Team tm{(int)threadIdx.x, kBwdNT, (int)threadIdx.x >> 5, kBwdWarps, 1, s_red, nullptr, nullptr};
-  const uint32_t start = first == 0xffffffffu ? cx.n_big : (first > cx.n_pairs ? cx.n_pairs : first);
   for (;;) {
-    if (threadIdx.x == 0) s_q = start + atomicAdd(&cx.hdr->q_bwd, 1u);
+    if (threadIdx.x == 0) s_q = atomicAdd(&cx.hdr->q_bwd, 1u);
     __syncthreads();
     const uint32_t qi = s_q;
     __syncthreads();
@@ -462,9 +461,15 @@ __global__ void __launch_bounds__(kBwdNT, 1) bwd_kernel(CallArgs a, uint32_t fir
   }
 }
 
-// The large pairs (queue[0, n_big)) on clusters of C CTAs: CTA 0 pulls a pair
-// and every CTA reads its index through distributed shared memory; cluster
-// c uses scratch slot c.
+// The whole batch on clusters of C CTAs.  First the large pairs
+// (queue[0, n_big)), each on a whole cluster: CTA 0 pulls a pair and every
+// CTA reads its index through distributed shared memory; cluster c uses the
+// scratch slot of its first CTA.  Then every CTA on its own takes the other
+// pairs (queue[n_big, n_pairs)) with its own slot; a cluster's CTAs leave
+// the first phase together (the pull that ends it is read between two
+// cluster barriers), so no slot is used by two teams at once.  One kernel
+// for both phases lets the small pairs fill SMs as soon as the large ones
+// are done.
 __global__ void __launch_bounds__(kBwdNT, 1) bwd_cluster_kernel(CallArgs a) {
   __shared__ __align__(16) float s_om[kMaxF];
   __shared__ float s_red[64];
@@ -476,26 +481,38 @@ __global__ void __launch_bounds__(kBwdNT, 1) bwd_cluster_kernel(CallArgs a) {
   const BwdCtx& cx = s_cx;
   const int C = (int)cl_size(), rank = (int)cl_rank();
   const uint32_t cid = cl_index();
-  if (cx.n_big == 0) return;  // the same on every CTA
   const uint64_t need = cx.hdr->bwd_slot_need;
   const uint64_t nslots = need ? cx.slots_bytes / need : 0;
   if (nslots == 0) {
-    if (cid == 0 && rank == 0 && threadIdx.x == 0) set_status(cx.hdr, 2 /* CF_ERR_WORKSPACE */, -1);
+    if (cid == 0 && rank == 0 && threadIdx.x == 0 && cx.n_pairs > 0) set_status(cx.hdr, 2 /* CF_ERR_WORKSPACE */, -1);
     return;
   }
-  if (cid >= nslots) return;  // the whole cluster
   if ((int)threadIdx.x < C) s_paddr[threadIdx.x] = cl_map(s_part, threadIdx.x);
   if (threadIdx.x == 0) s_qaddr = cl_map(&s_q, 0);
   __syncthreads();
-  float* slot = reinterpret_cast<float*>(cx.slots + (size_t)cid * need);
-  const Team tm{rank * kBwdNT + (int)threadIdx.x, C * kBwdNT, rank * kBwdWarps + ((int)threadIdx.x >> 5), C * kBwdWarps,
-                C, s_red, s_part, s_paddr};
+  const uint64_t first_cta = (uint64_t)blockIdx.x - rank;  // the cluster's CTA 0
+  if (cx.n_big > 0 && first_cta < nslots) {  // the same on every CTA of the cluster
+    float* slot = reinterpret_cast<float*>(cx.slots + first_cta * need);
+    const Team tm{rank * kBwdNT + (int)threadIdx.x, C * kBwdNT, rank * kBwdWarps + ((int)threadIdx.x >> 5),
+                  C * kBwdWarps, C, s_red, s_part, s_paddr};
+    for (;;) {
+      if (rank == 0 && threadIdx.x == 0) s_q = atomicAdd(&cx.hdr->q_bwd_big, 1u);
+      cl_sync();
+      const uint32_t qi = cl_ld_u32(s_qaddr);
+      cl_sync();  // CTA 0 overwrites s_q only after every CTA has read it
+      if (qi >= cx.n_big) break;
+      run_pair_bwd(cx, bwd_pair(cx, qi), slot, tm);
+    }
+  }
+  if (blockIdx.x >= nslots) return;
+  float* slot = reinterpret_cast<float*>(cx.slots + (uint64_t)blockIdx.x * need);
+  const Team tm{(int)threadIdx.x, kBwdNT, (int)threadIdx.x >> 5, kBwdWarps, 1, s_red, nullptr, nullptr};
   for (;;) {
-    if (rank == 0 && threadIdx.x == 0) s_q = atomicAdd(&cx.hdr->q_bwd_big, 1u);
-    cl_sync();
-    const uint32_t qi = cl_ld_u32(s_qaddr);
-    cl_sync();  // CTA 0 overwrites s_q only after every CTA has read it
-    if (qi >= cx.n_big) break;
+    if (threadIdx.x == 0) s_q = cx.n_big + atomicAdd(&cx.hdr->q_bwd, 1u);
+    __syncthreads();
+    const uint32_t qi = s_q;
+    __syncthreads();
+    if (qi >= cx.n_pairs) break;
     run_pair_bwd(cx, bwd_pair(cx, qi), slot, tm);
   }
 }
@@ -566,16 +583,15 @@ cudaError_t launch_backward(const CallArgs& a, cudaStream_t s) {
     g_bwd_clusters = n;
   }
   bwd_zero_kernel<<<2 * g_bwd_sm, 256, 0, s>>>(a);
-  uint32_t first = 0;
-  if (g_bwd_clusters > 0) {  // the large pairs first, each on a cluster
+  if (g_bwd_clusters > 0) {  // large pairs on clusters, then the rest CTA by CTA, in one kernel
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = bwd_cluster_cfg(g_bwd_clusters, attr, s);
     const cudaError_t e = cudaLaunchKernelEx(&cfg, bwd_cluster_kernel, a);
     if (e != cudaSuccess) return e;
-    first = 0xffffffffu;  // the CTA kernel starts after them (n_big, read on the device)
+  } else {  // no cluster fits: every pair on one CTA
+    const int grid = a.P < 2 * g_bwd_sm ? a.P : 2 * g_bwd_sm;
+    bwd_kernel<<<grid, kBwdNT, 0, s>>>(a);
   }
-  const int grid = a.P < 2 * g_bwd_sm ? a.P : 2 * g_bwd_sm;
-  bwd_kernel<<<grid, kBwdNT, 0, s>>>(a, first);
   if (a.grad_w_a) bwd_scatter_kernel<<<2 * g_bwd_sm, 256, 0, s>>>(a, 0);
   if (a.grad_w_b && a.pack_a != a.pack_b) bwd_scatter_kernel<<<2 * g_bwd_sm, 256, 0, s>>>(a, 1);
   return cudaGetLastError();
