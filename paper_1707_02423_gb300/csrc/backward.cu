@@ -129,31 +129,36 @@ __device__ __forceinline__ float gather_mem(const float* Y, const BwdPair& q, in
   return s;
 }
 
-// One forward step from X (normalised) into Xn:  Y = alpha/2 M(X) + (1-alpha) Ehat,
-// Xn = Y / |Y| (or Y).  Returns |Y| (1 when not renormalised).
-__device__ __forceinline__ float fwd_step(const BwdCtx& cx, const BwdPair& q, const float* X, float* Xn, const float* eh,
-                                          const Team& tm, int& par) {
+// One forward step with the normalisation carried, not applied: the stored
+// iterates are Y_k (X_k = Y_k / |Y_k|), so from Y and inv = 1 / |Y| (1 for
+// X_0 = Ehat, and always 1 when not renormalised) this writes
+//   Yn = alpha/2 M(Y) inv + (1-alpha) Ehat
+// and returns |Yn| (1 when not renormalised).  One pass, one team barrier.
+__device__ __forceinline__ float fwd_step(const BwdCtx& cx, const BwdPair& q, const float* Y, float inv, float* Yn,
+                                          const float* eh, const Team& tm, int& par) {
   const int lane = threadIdx.x & 31;
-  const float ca = 0.5f * cx.alpha, cb = 1.f - cx.alpha;
+  const float ca = 0.5f * cx.alpha * inv, cb = 1.f - cx.alpha;
   float ss = 0.f;
   for (int i = tm.warp; i < q.na; i += tm.nwarps)
     for (int j = lane; j < q.nb; j += 32) {
       const size_t o = (size_t)i * q.nb + j;
-      const float y = fmaf(ca, gather_mem(X, q, i, j), cb * eh[o]);
-      Xn[o] = y;
+      const float y = fmaf(ca, gather_mem(Y, q, i, j), cb * eh[o]);
+      Yn[o] = y;
       ss = fmaf(y, y, ss);
     }
   const float yy = tm.sum(ss, par);
   par ^= 1;
-  if (cx.norm_mode != 0) return 1.f;
-  const float nY = sqrtf(yy), inv = 1.f / nY;
-  for (int i = tm.warp; i < q.na; i += tm.nwarps)
-    for (int j = lane; j < q.nb; j += 32) Xn[(size_t)i * q.nb + j] *= inv;
-  tm.sync();
-  return nY;
+  return cx.norm_mode != 0 ? 1.f : sqrtf(yy);
 }
 
-__device__ __forceinline__ void run_pair_bwd(const BwdCtx& cx, const BwdPair& q, float* slot, const Team& tm) {
+// Shared-memory accumulators of the B-edge gradients per CTA (floats): a
+// pair whose B graph has more distinct edges uses a second sweep instead.
+constexpr int kBwdEdgeAcc = 16384;
+
+// gacc: this CTA's shared-memory accumulators of the B-edge gradients
+// (kBwdEdgeAcc floats).
+__device__ __forceinline__ void run_pair_bwd(const BwdCtx& cx, const BwdPair& q, float* slot, const Team& tm,
+                                             float* gacc) {
   const int t = tm.rank, lane = threadIdx.x & 31, w = tm.warp;
   const int TN = tm.size, TW = tm.nwarps;
   const int na = q.na, nb = q.nb;
@@ -182,6 +187,7 @@ __device__ __forceinline__ void run_pair_bwd(const BwdCtx& cx, const BwdPair& q,
   float* gb = bw + q.eb;
   float* Rf = gb + q.eb;  // [na][Fp]: sum_j Ebar_ij b_jf / c_j
   int par = 0;
+  float d_next = 0.f;  // <Xbar, X> of the adjoint step to come
 
   // both graphs' edge lists (CFG-local distinct-edge order), zeroed accumulators
   for (int i = t; i < na; i += TN)
@@ -229,86 +235,106 @@ __device__ __forceinline__ void run_pair_bwd(const BwdCtx& cx, const BwdPair& q,
   if (t == 0) nrm[0] = 1.f;
   tm.sync();
 
-  // forward, keeping X every S steps
-  const float* X = ck;
-  for (int k = 0; k < K; ++k) {
-    float* dst = ((k + 1) % S == 0) ? ck + (size_t)((k + 1) / S) * E : sg + (size_t)((k + 1) % S) * E;
-    const float nY = fwd_step(cx, q, X, dst, eh, tm, par);
-    if (t == 0) nrm[k + 1] = nY;
-    X = dst;
-  }
-  // Xbar_K = g 1[matched], Ehatbar = 0
-  for (int i = w; i < na; i += TW)
-    for (int j = lane; j < nb; j += 32) {
-      const size_t o = (size_t)i * nb + j;
-      xb[o] = 0.f;
-      ehb[o] = 0.f;
+  // forward, keeping Y every S steps (|Y_k| in nrm[k])
+  {
+    const float* Y = ck;
+    float inv = 1.f;
+    for (int k = 0; k < K; ++k) {
+      float* dst = ((k + 1) % S == 0) ? ck + (size_t)((k + 1) / S) * E : sg + (size_t)((k + 1) % S) * E;
+      const float nY = fwd_step(cx, q, Y, inv, dst, eh, tm, par);
+      if (t == 0) nrm[k + 1] = nY;
+      inv = 1.f / nY;
+      Y = dst;
     }
-  tm.sync();
-  const float g = cx.gbar[q.p];
-  for (int i = t; i < na; i += TN) {
-    const int m = cx.match[cx.m_off[q.p] + i];
-    if (m >= 0 && m < nb) xb[(size_t)i * nb + m] = g;
+    // Xbar_K = g 1[matched], Ehatbar = 0, and d = <Xbar_K, X_K> for the first adjoint step
+    for (int i = w; i < na; i += TW)
+      for (int j = lane; j < nb; j += 32) {
+        const size_t o = (size_t)i * nb + j;
+        xb[o] = 0.f;
+        ehb[o] = 0.f;
+      }
+    tm.sync();
+    const float g = cx.gbar[q.p];
+    float acc = 0.f;
+    for (int i = t; i < na; i += TN) {
+      const int m = cx.match[cx.m_off[q.p] + i];
+      if (m >= 0 && m < nb) {
+        xb[(size_t)i * nb + m] = g;
+        acc = fmaf(g, Y[(size_t)i * nb + m], acc);
+      }
+    }
+    d_next = tm.sum(acc, par) * inv;  // also orders the xb writes
+    par ^= 1;
   }
-  tm.sync();
+  // the B-edge gradient partials of this CTA (the edge loop computes each
+  // (A edge, B edge) term once for both graphs' gradients)
+  const bool eacc = q.eb <= kBwdEdgeAcc;
+  if (eacc)
+    for (int f = threadIdx.x; f < q.eb; f += kBwdNT) gacc[f] = 0.f;
 
-  // adjoint sweep, one segment at a time from the last
+  // adjoint sweep, one segment at a time from the last; two team barriers per step
   for (int seg = (K - 1) / S; seg >= 0 && K > 0; --seg) {
     const int k0 = seg * S, k1 = min(K, k0 + S);
     for (int i = w; i < na; i += TW)
       for (int j = lane; j < nb; j += 32) sg[(size_t)i * nb + j] = ck[(size_t)seg * E + (size_t)i * nb + j];
     tm.sync();
-    for (int k = k0; k < k1 - 1; ++k) fwd_step(cx, q, sg + (size_t)(k - k0) * E, sg + (size_t)(k - k0 + 1) * E, eh, tm, par);
-    // the segment's last iterate X_{k1} is the next checkpoint (or X_K)
-    const float* Xend = (k1 % S == 0) ? ck + (size_t)(k1 / S) * E : sg + (size_t)(k1 - k0) * E;
-    if (k1 % S != 0) fwd_step(cx, q, sg + (size_t)(k1 - 1 - k0) * E, sg + (size_t)(k1 - k0) * E, eh, tm, par);
+    for (int k = k0; k < k1 - 1; ++k)
+      fwd_step(cx, q, sg + (size_t)(k - k0) * E, 1.f / nrm[k], sg + (size_t)(k - k0 + 1) * E, eh, tm, par);
+    // the segment's last iterate Y_{k1} is the next checkpoint (or Y_K)
+    const float* Yend = (k1 % S == 0) ? ck + (size_t)(k1 / S) * E : sg + (size_t)(k1 - k0) * E;
+    if (k1 % S != 0) fwd_step(cx, q, sg + (size_t)(k1 - 1 - k0) * E, 1.f / nrm[k1 - 1], sg + (size_t)(k1 - k0) * E, eh, tm, par);
     for (int k = k1 - 1; k >= k0; --k) {
-      const float* X1 = (k + 1 == k1) ? Xend : sg + (size_t)(k + 1 - k0) * E;
-      const float* Xk = sg + (size_t)(k - k0) * E;
-      float d = 0.f;
-      if (cx.norm_mode == 0) {
-        float acc = 0.f;
-        for (int i = w; i < na; i += TW)
-          for (int j = lane; j < nb; j += 32) acc = fmaf(xb[(size_t)i * nb + j], X1[(size_t)i * nb + j], acc);
-        d = tm.sum(acc, par);
-        par ^= 1;
-      }
-      const float invY = cx.norm_mode == 0 ? 1.f / nrm[k + 1] : 1.f;
+      const float* Y1 = (k + 1 == k1) ? Yend : sg + (size_t)(k + 1 - k0) * E;
+      const float* Yk = sg + (size_t)(k - k0) * E;
+      const bool nrmz = cx.norm_mode == 0;
+      const float inv1 = nrmz ? 1.f / nrm[k + 1] : 1.f, invk = nrmz ? 1.f / nrm[k] : 1.f;
+      // Ybar = (Xbar - <Xbar, X_{k+1}> X_{k+1}) / |Y_{k+1}|;  Ehatbar += (1-alpha) Ybar;  Zbar = alpha Ybar
+      const float dd = nrmz ? d_next * inv1 : 0.f;
       for (int i = w; i < na; i += TW)
         for (int j = lane; j < nb; j += 32) {
           const size_t o = (size_t)i * nb + j;
-          const float yb = (xb[o] - d * X1[o]) * invY;
+          const float yb = (xb[o] - dd * Y1[o]) * inv1;
           ehb[o] = fmaf(1.f - cx.alpha, yb, ehb[o]);
           zb[o] = cx.alpha * yb;
         }
       tm.sync();
-      // edge gradients at this step
+      // edge gradients at this step, from X_k = Yk invk
       for (int e = w; e < q.ea; e += TW) {
         const int p = asrc[e], qq = adst[e];
+        const float we = aw[e] * invk;
         float s = 0.f;
         for (int f = lane; f < q.eb; f += 32) {
           const int j = bsrc[f], v = bdst[f];
-          const float T = fmaf(zb[(size_t)p * nb + j], Xk[(size_t)qq * nb + v], Xk[(size_t)p * nb + j] * zb[(size_t)qq * nb + v]);
+          const float T = fmaf(zb[(size_t)p * nb + j], Yk[(size_t)qq * nb + v], Yk[(size_t)p * nb + j] * zb[(size_t)qq * nb + v]);
           s = fmaf(bw[f], T, s);
+          if (eacc) atomicAdd(gacc + f, we * T);
         }
         s = warp_sum(s);
-        if (lane == 0) ga[e] = fmaf(0.5f, s, ga[e]);
+        if (lane == 0) ga[e] = fmaf(0.5f * invk, s, ga[e]);
       }
-      for (int f = w; f < q.eb; f += TW) {
-        const int j = bsrc[f], v = bdst[f];
-        float s = 0.f;
-        for (int e = lane; e < q.ea; e += 32) {
-          const int p = asrc[e], qq = adst[e];
-          const float T = fmaf(zb[(size_t)p * nb + j], Xk[(size_t)qq * nb + v], Xk[(size_t)p * nb + j] * zb[(size_t)qq * nb + v]);
-          s = fmaf(aw[e], T, s);
+      if (!eacc)
+        for (int f = w; f < q.eb; f += TW) {
+          const int j = bsrc[f], v = bdst[f];
+          float s = 0.f;
+          for (int e = lane; e < q.ea; e += 32) {
+            const int p = asrc[e], qq = adst[e];
+            const float T = fmaf(zb[(size_t)p * nb + j], Yk[(size_t)qq * nb + v], Yk[(size_t)p * nb + j] * zb[(size_t)qq * nb + v]);
+            s = fmaf(aw[e], T, s);
+          }
+          s = warp_sum(s);
+          if (lane == 0) gb[f] = fmaf(0.5f * invk, s, gb[f]);
         }
-        s = warp_sum(s);
-        if (lane == 0) gb[f] = fmaf(0.5f, s, gb[f]);
-      }
-      // Xbar_k = 1/2 M(Zbar)
+      // Xbar_k = 1/2 M(Zbar), and <Xbar_k, X_k> for the next step
+      float acc = 0.f;
       for (int i = w; i < na; i += TW)
-        for (int j = lane; j < nb; j += 32) xb[(size_t)i * nb + j] = 0.5f * gather_mem(zb, q, i, j);
-      tm.sync();
+        for (int j = lane; j < nb; j += 32) {
+          const size_t o = (size_t)i * nb + j;
+          const float x = 0.5f * gather_mem(zb, q, i, j);
+          xb[o] = x;
+          acc = fmaf(x, Yk[o], acc);
+        }
+      d_next = tm.sum(acc, par) * invk;  // a team barrier: Xbar_k complete
+      par ^= 1;
     }
   }
   // Ehatbar += Xbar_0
@@ -366,8 +392,12 @@ __device__ __forceinline__ void run_pair_bwd(const BwdCtx& cx, const BwdPair& q,
     }
   }
   // this pair's edge gradients into the packs' distinct-edge accumulators
+  // (the B-edge sums from each CTA's shared-memory partials)
   for (int e = t; e < q.ea; e += TN) atomicAdd(cx.gcan_a + q.a_edge0 + e, ga[e]);
-  for (int f = t; f < q.eb; f += TN) atomicAdd(cx.gcan_b + q.b_edge0 + f, gb[f]);
+  if (eacc)
+    for (int f = threadIdx.x; f < q.eb; f += kBwdNT) atomicAdd(cx.gcan_b + q.b_edge0 + f, 0.5f * gacc[f]);
+  else
+    for (int f = t; f < q.eb; f += TN) atomicAdd(cx.gcan_b + q.b_edge0 + f, gb[f]);
   tm.sync();
 }
 
@@ -436,6 +466,7 @@ __device__ __forceinline__ BwdPair bwd_pair(const BwdCtx& cx, uint32_t qi) {
 // One CTA per pair, every pair of the queue (used when no cluster of
 // kBwdCluster CTAs fits on the device).
 __global__ void __launch_bounds__(kBwdNT, 1) bwd_kernel(CallArgs a) {
+  extern __shared__ __align__(16) float s_gacc[];  // kBwdEdgeAcc floats
   __shared__ __align__(16) float s_om[kMaxF];
   __shared__ float s_red[64];
   __shared__ BwdCtx s_cx;
@@ -457,7 +488,7 @@ __global__ void __launch_bounds__(kBwdNT, 1) bwd_kernel(CallArgs a) {
     const uint32_t qi = s_q;
     __syncthreads();
     if (qi >= cx.n_pairs) break;
-    run_pair_bwd(cx, bwd_pair(cx, qi), slot, tm);
+    run_pair_bwd(cx, bwd_pair(cx, qi), slot, tm, s_gacc);
   }
 }
 
@@ -471,6 +502,7 @@ __global__ void __launch_bounds__(kBwdNT, 1) bwd_kernel(CallArgs a) {
 // for both phases lets the small pairs fill SMs as soon as the large ones
 // are done.
 __global__ void __launch_bounds__(kBwdNT, 1) bwd_cluster_kernel(CallArgs a) {
+  extern __shared__ __align__(16) float s_gacc[];  // kBwdEdgeAcc floats
   __shared__ __align__(16) float s_om[kMaxF];
   __shared__ float s_red[64];
   __shared__ float s_part[2];
@@ -501,7 +533,7 @@ __global__ void __launch_bounds__(kBwdNT, 1) bwd_cluster_kernel(CallArgs a) {
       const uint32_t qi = cl_ld_u32(s_qaddr);
       cl_sync();  // CTA 0 overwrites s_q only after every CTA has read it
       if (qi >= cx.n_big) break;
-      run_pair_bwd(cx, bwd_pair(cx, qi), slot, tm);
+      run_pair_bwd(cx, bwd_pair(cx, qi), slot, tm, s_gacc);
     }
   }
   if (blockIdx.x >= nslots) return;
@@ -513,7 +545,7 @@ __global__ void __launch_bounds__(kBwdNT, 1) bwd_cluster_kernel(CallArgs a) {
     const uint32_t qi = s_q;
     __syncthreads();
     if (qi >= cx.n_pairs) break;
-    run_pair_bwd(cx, bwd_pair(cx, qi), slot, tm);
+    run_pair_bwd(cx, bwd_pair(cx, qi), slot, tm, s_gacc);
   }
 }
 
@@ -548,6 +580,7 @@ int g_bwd_sm = 0;
 int g_bwd_clusters = -1;  // resident clusters of kBwdCluster CTAs, 0 if none fit
 
 constexpr int kBwdCluster = 8;
+constexpr size_t kBwdSmem = sizeof(float) * kBwdEdgeAcc;
 
 cudaLaunchConfig_t bwd_cluster_cfg(int n_clusters, cudaLaunchAttribute* attr, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
@@ -557,7 +590,7 @@ cudaLaunchConfig_t bwd_cluster_cfg(int n_clusters, cudaLaunchAttribute* attr, cu
   attr[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3(n_clusters * kBwdCluster, 1, 1);
   cfg.blockDim = dim3(kBwdNT, 1, 1);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = kBwdSmem;
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
@@ -575,6 +608,10 @@ cudaError_t launch_backward(const CallArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
   }
   if (g_bwd_clusters < 0) {
+    cudaError_t e = cudaFuncSetAttribute(bwd_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdSmem);
+    if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = bwd_cluster_cfg(1, attr, s);
     int n = 0;
@@ -590,7 +627,7 @@ cudaError_t launch_backward(const CallArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
   } else {  // no cluster fits: every pair on one CTA
     const int grid = a.P < 2 * g_bwd_sm ? a.P : 2 * g_bwd_sm;
-    bwd_kernel<<<grid, kBwdNT, 0, s>>>(a);
+    bwd_kernel<<<grid, kBwdNT, kBwdSmem, s>>>(a);
   }
   if (a.grad_w_a) bwd_scatter_kernel<<<2 * g_bwd_sm, 256, 0, s>>>(a, 0);
   if (a.grad_w_b && a.pack_a != a.pack_b) bwd_scatter_kernel<<<2 * g_bwd_sm, 256, 0, s>>>(a, 1);
