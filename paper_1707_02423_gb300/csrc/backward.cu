@@ -97,31 +97,30 @@ struct BwdCtx {
   float alpha;
   int K, norm_mode, F, Fp;
   uint32_t n_pairs;  // valid pairs in the queue
-  uint32_t n_big;    // the leading pairs that take a cluster when clusters are launched
 };
 
-// Successor-pair plus predecessor-pair sum of Y at entry (i, j), both graphs'
-// lists read from the pack (A indexes rows, B columns; ld = n_b).
+// Successor-pair plus predecessor-pair sum of Y at entry (i, j) (A indexes
+// rows, B columns; ld = n_b), both graphs' lists read from the pack.
 __device__ __forceinline__ float gather_mem(const float* Y, const BwdPair& q, int i, int j) {
   float s = 0.f;
-  const int c0 = __ldg(q.bo + j), c1 = __ldg(q.bo + j + 1);
-  for (int e = __ldg(q.ao + i), e1 = __ldg(q.ao + i + 1); e < e1; ++e) {
-    const CfAdj a = ldg_adj(q.aoa + e);
+  const int c0 = q.bo[j], c1 = q.bo[j + 1];
+  for (int e = q.ao[i], e1 = q.ao[i + 1]; e < e1; ++e) {
+    const CfAdj a = q.aoa[e];
     const float* row = Y + (size_t)a.nbr * q.nb;
     float t = 0.f;
     for (int f = c0; f < c1; ++f) {
-      const CfAdj b = ldg_adj(q.boa + f);
+      const CfAdj b = q.boa[f];
       t = fmaf(b.w, row[b.nbr], t);
     }
     s = fmaf(a.w, t, s);
   }
-  const int d0 = __ldg(q.bi + j), d1 = __ldg(q.bi + j + 1);
-  for (int e = __ldg(q.ai + i), e1 = __ldg(q.ai + i + 1); e < e1; ++e) {
-    const CfAdj a = ldg_adj(q.aia + e);
+  const int d0 = q.bi[j], d1 = q.bi[j + 1];
+  for (int e = q.ai[i], e1 = q.ai[i + 1]; e < e1; ++e) {
+    const CfAdj a = q.aia[e];
     const float* row = Y + (size_t)a.nbr * q.nb;
     float t = 0.f;
     for (int f = d0; f < d1; ++f) {
-      const CfAdj b = ldg_adj(q.bia + f);
+      const CfAdj b = q.bia[f];
       t = fmaf(b.w, row[b.nbr], t);
     }
     s = fmaf(a.w, t, s);
@@ -375,20 +374,21 @@ __device__ __forceinline__ void run_pair_bwd(const BwdCtx& cx, const BwdPair& q,
       if (lane == 0) gam[j] = s;
     }
     tm.sync();
-    for (int f = t; f < cx.F; f += TN) {
+    for (int f = w; f < cx.F; f += TW) {  // a warp per feature
       float g1 = 0.f, g2 = 0.f, g3 = 0.f;
-      for (int i = 0; i < na; ++i)
+      for (int i = lane; i < na; i += 32)
         if (rn[i] > 0.f) {
           const float a = __ldg(q.aat + (size_t)i * cx.Fp + f);
           g1 = fmaf(a / rn[i], Rf[(size_t)i * cx.Fp + f], g1);
           g2 = fmaf(a * a / (2.f * rn[i] * rn[i]), rho[i], g2);
         }
-      for (int j = 0; j < nb; ++j)
+      for (int j = lane; j < nb; j += 32)
         if (cn[j] > 0.f) {
           const float b = __ldg(q.bat + (size_t)j * cx.Fp + f);
           g3 = fmaf(b * b / (2.f * cn[j] * cn[j]), gam[j], g3);
         }
-      atomicAdd(cx.gomega + f, g1 - g2 - g3);
+      const float gsum = warp_sum(g1 - g2 - g3);
+      if (lane == 0) atomicAdd(cx.gomega + f, gsum);
     }
   }
   // this pair's edge gradients into the packs' distinct-edge accumulators
@@ -431,8 +431,6 @@ __device__ __forceinline__ void bwd_setup(const CallArgs& a, BwdCtx& c, float* s
     uint32_t n = 0;
     for (int k = 0; k < kNumClasses; ++k) n += c.hdr->n_class[k];
     c.n_pairs = n;
-    // the pairs that fit no single CTA's shared memory in the forward lead the queue
-    c.n_big = c.hdr->n_class[kClassGlobal] + c.hdr->n_class[kClassCluster];
   }
   __syncthreads();
   if (threadIdx.x < kMaxF) s_om[threadIdx.x] = threadIdx.x < c.F ? a.omega[threadIdx.x] : 0.f;
@@ -463,6 +461,13 @@ __device__ __forceinline__ BwdPair bwd_pair(const BwdCtx& cx, uint32_t qi) {
   return q;
 }
 
+// Pairs of at least this many entries take a whole cluster when clusters are
+// launched (a pair's adjoint is a serial chain of sweeps over its entries,
+// so the largest pairs need the widest teams); the others one CTA each.
+constexpr int64_t kBwdBigEntries = 16384;
+
+__device__ __forceinline__ bool bwd_big(const BwdPair& q) { return (int64_t)q.na * q.nb >= kBwdBigEntries; }
+
 // One CTA per pair, every pair of the queue (used when no cluster of
 // kBwdCluster CTAs fits on the device).
 __global__ void __launch_bounds__(kBwdNT, 1) bwd_kernel(CallArgs a) {
@@ -492,15 +497,15 @@ __global__ void __launch_bounds__(kBwdNT, 1) bwd_kernel(CallArgs a) {
   }
 }
 
-// The whole batch on clusters of C CTAs.  First the large pairs
-// (queue[0, n_big)), each on a whole cluster: CTA 0 pulls a pair and every
-// CTA reads its index through distributed shared memory; cluster c uses the
-// scratch slot of its first CTA.  Then every CTA on its own takes the other
-// pairs (queue[n_big, n_pairs)) with its own slot; a cluster's CTAs leave
-// the first phase together (the pull that ends it is read between two
-// cluster barriers), so no slot is used by two teams at once.  One kernel
-// for both phases lets the small pairs fill SMs as soon as the large ones
-// are done.
+// The whole batch on clusters of C CTAs.  First the large pairs (bwd_big,
+// in queue order), each on a whole cluster: CTA 0 pulls a queue position and
+// every CTA reads it through distributed shared memory, so all of them skip
+// or take the same pairs; cluster c uses the scratch slot of its first CTA.
+// Then every CTA on its own takes the other pairs with its own slot; a
+// cluster's CTAs leave the first phase together (the pull that ends it is
+// read between two cluster barriers), so no slot is used by two teams at
+// once.  One kernel for both phases lets the small pairs fill SMs as soon as
+// the large ones are done.
 __global__ void __launch_bounds__(kBwdNT, 1) bwd_cluster_kernel(CallArgs a) {
   extern __shared__ __align__(16) float s_gacc[];  // kBwdEdgeAcc floats
   __shared__ __align__(16) float s_om[kMaxF];
@@ -523,7 +528,7 @@ __global__ void __launch_bounds__(kBwdNT, 1) bwd_cluster_kernel(CallArgs a) {
   if (threadIdx.x == 0) s_qaddr = cl_map(&s_q, 0);
   __syncthreads();
   const uint64_t first_cta = (uint64_t)blockIdx.x - rank;  // the cluster's CTA 0
-  if (cx.n_big > 0 && first_cta < nslots) {  // the same on every CTA of the cluster
+  if (first_cta < nslots) {  // the same on every CTA of the cluster
     float* slot = reinterpret_cast<float*>(cx.slots + first_cta * need);
     const Team tm{rank * kBwdNT + (int)threadIdx.x, C * kBwdNT, rank * kBwdWarps + ((int)threadIdx.x >> 5),
                   C * kBwdWarps, C, s_red, s_part, s_paddr};
@@ -532,20 +537,22 @@ __global__ void __launch_bounds__(kBwdNT, 1) bwd_cluster_kernel(CallArgs a) {
       cl_sync();
       const uint32_t qi = cl_ld_u32(s_qaddr);
       cl_sync();  // CTA 0 overwrites s_q only after every CTA has read it
-      if (qi >= cx.n_big) break;
-      run_pair_bwd(cx, bwd_pair(cx, qi), slot, tm, s_gacc);
+      if (qi >= cx.n_pairs) break;
+      const BwdPair q = bwd_pair(cx, qi);
+      if (bwd_big(q)) run_pair_bwd(cx, q, slot, tm, s_gacc);
     }
   }
   if (blockIdx.x >= nslots) return;
   float* slot = reinterpret_cast<float*>(cx.slots + (uint64_t)blockIdx.x * need);
   const Team tm{(int)threadIdx.x, kBwdNT, (int)threadIdx.x >> 5, kBwdWarps, 1, s_red, nullptr, nullptr};
   for (;;) {
-    if (threadIdx.x == 0) s_q = cx.n_big + atomicAdd(&cx.hdr->q_bwd, 1u);
+    if (threadIdx.x == 0) s_q = atomicAdd(&cx.hdr->q_bwd, 1u);
     __syncthreads();
     const uint32_t qi = s_q;
     __syncthreads();
     if (qi >= cx.n_pairs) break;
-    run_pair_bwd(cx, bwd_pair(cx, qi), slot, tm, s_gacc);
+    const BwdPair q = bwd_pair(cx, qi);
+    if (!bwd_big(q)) run_pair_bwd(cx, q, slot, tm, s_gacc);
   }
 }
 
