@@ -325,6 +325,11 @@ cf_status cf_autotune_ws_size(const void* h_pack_a, const void* h_pack_b, const 
  * matchings) under every tune on a deterministic sample of at most 16384 of
  * the pairs (pair floor(k P / S), k < S), one warm-up and three timed calls
  * each, and return the fastest in *tune (its time in *best_ms, may be NULL).
+ * When one call of the default tune on the sample takes over 40 ms, the
+ * candidates are timed on an evenly strided part of it that fits 40 ms; over
+ * 160 ms (pairs of hundreds to thousands of blocks), on the whole sample,
+ * once each, and only the thread counts and cluster sizes (smallest group a
+ * warp, matching policy 1), the other choices not mattering for such pairs.
  * The choice is cached in the text file cache_path (or, when NULL, in the file
  * named by the environment variable CF_AUTOTUNE_CACHE; no caching if neither
  * is set) under a key of device name, SM count, F_pad, K, norm_mode and the

@@ -257,7 +257,13 @@ cf_status cf_autotune(const void* h_pack_a, const void* h_pack_b, const void* d_
   int St = S;
   float ms0 = 0.f;
   s = timed(1, St, &ms0);
-  if (s == CF_OK && ms0 > kTuneBudgetMs && St > kTuneMinPairs) {
+  // far over the budget (pairs of hundreds to thousands of blocks): only the
+  // thread count and the cluster size matter (such pairs are never
+  // shared-memory resident), and the sample is not cut, because a part of it
+  // that the device runs in one or two waves favours wide teams (clusters)
+  // that lose on the whole batch; one timed call per candidate
+  const bool coarse = ms0 > 4.f * kTuneBudgetMs;
+  if (s == CF_OK && !coarse && ms0 > kTuneBudgetMs && St > kTuneMinPairs) {
     const int S2 = std::max(kTuneMinPairs, (int)(St * (kTuneBudgetMs / ms0)));
     std::vector<int32_t> sub(2 * (size_t)S2);
     for (int k = 0; k < S2; ++k) {
@@ -273,11 +279,15 @@ cf_status cf_autotune(const void* h_pack_a, const void* h_pack_b, const void* d_
   int best_t = 0;
   float best = 1e30f;
   for (int t = 1; t <= kNumTunes && s == CF_OK; ++t) {
+    if (coarse) {  // smallest group a warp, ranked lists in groups of at most a quarter CTA
+      const Tune d = decode_tune(t);
+      if (d.min_cls != kClassWarp || d.ranked != 1) continue;
+    }
     float tmin = 1e30f;
-    for (int r = 0; r <= kTuneReps && s == CF_OK; ++r) {  // call 0 warms up
+    for (int r = 0; r <= (coarse ? 0 : kTuneReps) && s == CF_OK; ++r) {  // call 0 warms up
       float ms = 0.f;
       s = timed(t, St, &ms);
-      if (r > 0) tmin = std::min(tmin, ms);
+      if (r > 0 || coarse) tmin = std::min(tmin, ms);
     }
     if (s == CF_OK) s = cf_status_check(d_ws, stream);
     if (s == CF_OK && tmin < best) {
