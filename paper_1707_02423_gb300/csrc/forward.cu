@@ -297,45 +297,63 @@ __device__ __forceinline__ float gather_g(const float* Y, int ld, const Geo& g, 
 //
 // State per row (rb) and column (cb): >= 0 best live partner, -2 not yet
 // computed, -1 no candidate (only with NaN entries), <= -3 matched to -3 - v.
-// A round has two barriers:
+// A round has three barriers:
 //   A  every live row whose best column died (or was never computed) rescans
-//      the live columns, and every such column rescans the live rows (a warp
-//      per row / column).  Liveness changes only in B, so these scans agree.
+//      the live columns (a warp per row), and every live row stamps its best
+//      column with the round number in tg,
+//   A' every stamped column whose best row died (or was never computed)
+//      rescans the live rows.  A column no live row names cannot hold a
+//      locally dominant entry this round, so its best is not needed; X_K is
+//      close to rank one, so most rows name the same few columns and most
+//      column rescans are skipped.  Liveness changes only in B, so these
+//      scans agree, and a kept best stays right (bests only change when they
+//      die).
 //   B  every row whose best column names it back is matched; the round's
 //      matches are counted by a group sum.  A row's entry is written only by
 //      its own thread, a column's only by the thread of the row it names.
 // Every round matches at least one pair for finite X (the largest live entry
 // is locally dominant), so the loop is bounded by min(n_row, n_col) rounds; if
 // the bound is reached first (NaN in X) the status word gets CF_ERR_NUMERIC.
+// tg: n_col entries (round stamps, values up to min(n_row, n_col)).
 // Returns the score on every thread; writes match[n_a] if given.
 template <class IdxT, class Grp>
 __device__ __forceinline__ float greedy(const Grp& grp, const float* X, int ld, int n_row, int n_col, int tr,
-                                        IdxT* rb, IdxT* cb, int32_t* mo, WsHeader* hdr, int pidx) {
+                                        IdxT* rb, IdxT* cb, IdxT* tg, int32_t* mo, WsHeader* hdr, int pidx) {
   const int t = grp.rank, G = grp.size, lane = t & 31, w = grp.warp(), NW = grp.nwarps();
   for (int r = t; r < n_row; r += G) rb[r] = (IdxT)-2;
-  for (int c = t; c < n_col; c += G) cb[c] = (IdxT)-2;
+  for (int c = t; c < n_col; c += G) {
+    cb[c] = (IdxT)-2;
+    tg[c] = (IdxT)0;
+  }
   grp.sync();
   const int need = min(n_row, n_col);
   int matched = 0, par = 0;
   for (int round = 0; matched < need && round < need; ++round) {
+    const IdxT stamp = (IdxT)(round + 1);
     for (int r = w; r < n_row; r += NW) {
-      const int v = rb[r];
-      if (!(v == -2 || (v >= 0 && cb[v] <= (IdxT)-3))) continue;
-      float bv = -CUDART_INF_F;
-      int bi = 0x7fffffff;
-      const float* xr = X + (size_t)r * ld;
-      for (int c = lane; c < n_col; c += 32)
-        if (cb[c] > (IdxT)-3) {
-          const float x = xr[c];
-          if (x > bv) {
-            bv = x;
-            bi = c;
+      int v = rb[r];
+      if (v <= -3) continue;  // matched
+      if (v == -2 || (v >= 0 && cb[v] <= (IdxT)-3)) {
+        float bv = -CUDART_INF_F;
+        int bi = 0x7fffffff;
+        const float* xr = X + (size_t)r * ld;
+        for (int c = lane; c < n_col; c += 32)
+          if (cb[c] > (IdxT)-3) {
+            const float x = xr[c];
+            if (x > bv) {
+              bv = x;
+              bi = c;
+            }
           }
-        }
-      warp_argmax(bv, bi);
-      if (lane == 0) rb[r] = bi == 0x7fffffff ? (IdxT)-1 : (IdxT)bi;
+        warp_argmax(bv, bi);
+        v = bi == 0x7fffffff ? -1 : bi;
+        if (lane == 0) rb[r] = (IdxT)v;
+      }
+      if (lane == 0 && v >= 0) tg[v] = stamp;
     }
+    grp.sync();
     for (int c = w; c < n_col; c += NW) {
+      if (tg[c] != stamp) continue;  // no live row names it
       const int v = cb[c];
       if (!(v == -2 || (v >= 0 && rb[v] <= (IdxT)-3))) continue;
       float bv = -CUDART_INF_F;
@@ -726,7 +744,8 @@ __device__ __forceinline__ void run_pair_s(const Ctx& cx, const Geo& g, const Gr
       if (cx.scores && t == 0) cx.scores[g.p] = sc;
     } else {
       const float sc = greedy<int16_t>(grp, Xs, ld, s.n_row, s.n_col, s.tr, reinterpret_cast<int16_t*>(ehb),
-                                       reinterpret_cast<int16_t*>(freeb), mo, cx.hdr, g.p);
+                                       reinterpret_cast<int16_t*>(freeb), reinterpret_cast<int16_t*>(freeb) + s.n_col,
+                                       mo, cx.hdr, g.p);
       if (cx.scores && t == 0) cx.scores[g.p] = sc;
     }
   }
@@ -871,7 +890,7 @@ __device__ __noinline__ void run_pair_g(const Ctx& cx, const Geo& g, const Group
   if (cx.X) store_x(grp, cx, g, Xs, n_col);
   if (cx.scores || cx.match) {
     int32_t* mo = cx.match ? cx.match + cx.m_off[g.p] : nullptr;
-    const float sc = greedy<int32_t>(grp, Xs, n_col, n_row, n_col, 0, ms, ms + n_row, mo, cx.hdr, g.p);
+    const float sc = greedy<int32_t>(grp, Xs, n_col, n_row, n_col, 0, ms, ms + n_row, ms + n_row + n_col, mo, cx.hdr, g.p);
     if (cx.scores && t == 0) cx.scores[g.p] = sc;
   }
   grp.sync();
@@ -1272,7 +1291,8 @@ __device__ __noinline__ void run_pair_c(const Ctx& cx, const Geo& g, const Group
     const ClGroup cg{rank * G + t, C * G, C, &st};
     int32_t* ms = reinterpret_cast<int32_t*>(slot + (size_t)s.n_row * s.n_col);
     int32_t* mo = cx.match ? cx.match + cx.m_off[g.p] : nullptr;
-    const float sc = greedy<int32_t>(cg, slot, s.n_col, s.n_row, s.n_col, s.tr, ms, ms + s.n_row, mo, cx.hdr, g.p);
+    const float sc = greedy<int32_t>(cg, slot, s.n_col, s.n_row, s.n_col, s.tr, ms, ms + s.n_row,
+                                     ms + s.n_row + s.n_col, mo, cx.hdr, g.p);
     if (cx.scores && cg.rank == 0) cx.scores[g.p] = sc;
   }
 }
@@ -1364,7 +1384,7 @@ __global__ void __launch_bounds__(kMatchNT) match_only_kernel(CallArgs a) {
     const int nb = B.node_off[pb + 1] - B.node_off[pb];
     const float* X = a.X_in + x_off[p];
     int32_t* mo = a.match ? a.match + m_off[p] : nullptr;
-    const float sc = greedy<int16_t>(grp, X, nb, na, nb, 0, ms, ms + na, mo, hdr, p);
+    const float sc = greedy<int16_t>(grp, X, nb, na, nb, 0, ms, ms + na, ms + na + nb, mo, hdr, p);
     if (a.scores && threadIdx.x == 0) a.scores[p] = sc;
     __syncthreads();
   }
