@@ -283,13 +283,18 @@ def make_step(name, dev, tune_cache=None):
     out = {"scores": torch.empty(P, dtype=torch.float32, device=dev),
            "match": torch.empty(int(m_off[-1]), dtype=torch.int32, device=dev)}
     tune, _ = api.autotune(pa, pb, pairs_np, omega, ALPHA, K_ITERS, cache_path=tune_cache)
+    # kernels per forward call: the three plan kernels, the persistent forward
+    # and, under a cluster tune, the cluster-tier kernel; per adjoint call: the
+    # three plan kernels, the accumulator reset, the adjoint and the scatter
+    n_fwd = 4 + (1 if api.tune_info(tune)["cluster"] >= 2 else 0)
+    n_bwd = 3 + 1 + 1 + (1 if w.shared else 2)
     if name in ("cfg2", "cfg3"):
         ws_bytes = api.ws_size(pa, pb, pairs_np, prm)
 
         def step():
             api.similarity(pa, pb, pairs_np, omega, ALPHA, K_ITERS, want_match=True, ws=ws, d_pairs=d_pairs,
                            out=out, check_status=False, ws_bytes=ws_bytes, tune=tune)
-        return step, P, 4, tune
+        return step, P, n_fwd, tune
     if name == "cfg4":
         ws_bytes = api.ws_size(pa, pb, pairs_np, prm)
         bws = api.Workspace(dev)
@@ -299,7 +304,7 @@ def make_step(name, dev, tune_cache=None):
             api.similarity(pa, pb, pairs_np, omega, ALPHA, K_ITERS, want_match=True, ws=ws, d_pairs=d_pairs,
                            out=out, check_status=False, ws_bytes=ws_bytes, tune=tune)
             api.similarity_backward(pa, pb, pairs_np, omega, out["match"], g, ALPHA, K_ITERS, ws=bws)
-        return step, P, 4 + 7, tune
+        return step, P, n_fwd + n_bwd, tune
     # cfg5: scores of every query-corpus pair, top-16 per query, matchings of the winners
     nq, nc, k = w.meta["n_query"], w.meta["n_corpus"], w.meta["top_k"]
     ws_bytes = api.ws_size(pa, pb, pairs_np, prm)
@@ -311,7 +316,7 @@ def make_step(name, dev, tune_cache=None):
         top, idx = api.topk(out["scores"].view(nq, nc), k)
         win = np.stack([np.repeat(np.arange(nq), k), idx.cpu().numpy().ravel()], axis=1).astype(np.int32)
         api.similarity(pa, pb, win, omega, ALPHA, K_ITERS, want_match=True, ws=mws, check_status=False, tune=tune)
-    return step, P, 4 + 1 + 4, tune
+    return step, P, n_fwd + 1 + n_fwd, tune
 
 
 def run_workload(args):
@@ -515,7 +520,9 @@ def run_ours(args):
                 "ms_per_step": e2e_s * 1e3,
                 "what": "cf_pack_cfgs (host build + copy) + pinned pair upload + cf_similarity + pinned "
                         "readback of scores and matchings, wall clock"},
-        "gpu_launches": 4 * args.steps,
+        # per step: the three plan kernels, the persistent forward, and the
+        # cluster-tier kernel when the tune has one
+        "gpu_launches": (4 + (1 if api.tune_info(tune)["cluster"] >= 2 else 0)) * args.steps,
         "clocks": clk,
         "wall_s_timed_region": t_wall,
     }
