@@ -102,7 +102,8 @@ uint64_t fnv1a(const std::string& s) {
   return h;
 }
 
-// Cache key: device, SM count, attribute stride, K, normalisation, and the
+// Cache key: the size of the tune table (ids mean other configurations when
+// it changes), device, SM count, attribute stride, K, normalisation, and the
 // sample's distribution over cost buckets (two per octave of the
 // per-iteration work), each bucket's share rounded to 1/32.
 std::string tune_key(const PackHost& A, const PackHost& B, const std::vector<int32_t>& sp, const cf_params* prm) {
@@ -127,8 +128,8 @@ std::string tune_key(const PackHost& A, const PackHost& B, const std::vector<int
   for (char& c : name)
     if (c == ' ' || c == '\t') c = '_';
   char buf[512];
-  snprintf(buf, sizeof buf, "abi2c;dev=%s;sm=%d;Fp=%d;K=%d;norm=%d;sig=%016llx", name.c_str(), prop.multiProcessorCount,
-           A.h.F_pad, prm->K, prm->norm_mode, (unsigned long long)fnv1a(sig));
+  snprintf(buf, sizeof buf, "abi2c;tunes=%d;dev=%s;sm=%d;Fp=%d;K=%d;norm=%d;sig=%016llx", kNumTunes, name.c_str(),
+           prop.multiProcessorCount, A.h.F_pad, prm->K, prm->norm_mode, (unsigned long long)fnv1a(sig));
   return buf;
 }
 
