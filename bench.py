@@ -47,14 +47,23 @@ WORKLOADS = {
             "and the adjoint (edge-weight and omega gradients, sqrt(K) checkpoints)",
     "cfg5": "cfg5: 32 query CFGs x 10,000-CFG corpus (320,000 pairs), n log-uniform 5-400, F=25, K=40: "
             "scores, top-16 per query, then matchings of the 512 winners",
+    "dist": "Table 1 distances (Euclidean, Manhattan, Minkowski p=3, Jaccard, Cosine) of the bilinearly resized "
+            "transition matrices, min-max scaled to [0,1], for all 19,900 pairs of the 200 cfg2 CFGs",
+    "optimal": "cfg2 forward (all 19,900 pairs, K=40) with the maximum-weight assignment instead of the greedy "
+               "matching (X_K kept in HBM, one warp per pair)",
+    "ward": "Ward clustering of the 200 cfg2 CFGs: the 200 x 200 score matrix from the 19,900 pair scores, then "
+            "the Ward linkage of its rows (199 merges)",
 }
+# units of the per-workload lines (the headline and the other workloads: pairs/s)
+UNITS = {"ward": "linkages/s"}
 WORKLOAD = WORKLOADS["cfg2"]
 
 
 def workload(name="cfg2"):
     from gen import config2, config3, config4, config5
 
-    return {"cfg2": config2, "cfg3": config3, "cfg4": config4, "cfg5": config5}[name]()
+    return {"cfg2": config2, "cfg3": config3, "cfg4": config4, "cfg5": config5, "dist": config2,
+            "optimal": config2, "ward": config2}[name]()
 
 
 def algorithmic(w, K):
@@ -164,6 +173,42 @@ def cpu_oracle(w, seconds: float, seed: int = 0):
     return done / dt, done, dt
 
 
+def cpu_next(name, w, seconds: float):
+    """The oracle as it stands, single-threaded, on a bounded sample of the
+    distances / optimal-matching / Ward workload: (rate in the workload's
+    unit, count, seconds, sample description).  Ward's sample is the score
+    matrix and linkage of seeded synthetic scores (the same shape)."""
+    import oracle
+    from oracle import distances as odist
+    from oracle import ward as oward
+
+    rng = np.random.default_rng(0)
+    t0 = time.perf_counter()
+    done = 0
+    if name == "ward":
+        scores = rng.uniform(1.0, 1.3, len(w.pairs))
+        while True:
+            oward.linkage(oward.score_matrix(len(w.cfgs_a), w.pairs, scores))
+            done += 1
+            if time.perf_counter() - t0 >= seconds:
+                break
+        dt = time.perf_counter() - t0
+        return done / dt, done, dt, f"{done} score matrices + Ward linkages of 200 CFGs (seeded scores)"
+    order = rng.permutation(len(w.pairs))
+    om = np.ones(w.F)
+    for p in order:
+        a, b = w.pairs[p]
+        if name == "dist":
+            odist.pair_distances(w.cfgs_a[a], w.cfgs_b[b], 3.0)
+        else:
+            oracle.optimal_match(oracle.similarity(w.cfgs_a[a], w.cfgs_b[b], om, ALPHA, K_ITERS)["X"])
+        done += 1
+        if time.perf_counter() - t0 >= seconds and done >= 20:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt, f"{done} seeded random pairs of the workload, single-threaded FP64 oracle"
+
+
 def dist_setup(n_gpus):
     import torch
 
@@ -265,6 +310,8 @@ def timed_steps(step, steps, warmup, flush, stream):
 def make_step(name, dev, tune_cache=None):
     """The step of one workload through the Python API (kernel configuration
     from the autotuner): returns (step, n_pairs, launches_per_step, tune)."""
+    import ctypes as C
+
     import torch
 
     from paper_1707_02423_gb300 import _binding as B
@@ -288,6 +335,46 @@ def make_step(name, dev, tune_cache=None):
     # three plan kernels, the accumulator reset, the adjoint and the scatter
     n_fwd = 4 + (1 if api.tune_info(tune)["cluster"] >= 2 else 0)
     n_bwd = 3 + 1 + 1 + (1 if w.shared else 2)
+    if name == "dist":  # the C ABI directly, every buffer allocated before the timed region
+        L = B.lib()
+        n = C.c_size_t(0)
+        B.check(L.cf_distances_ws_size(P, C.byref(n)))
+        dws = torch.empty(max(int(n.value), 256), dtype=torch.uint8, device=dev)
+        dout = torch.empty(P, 5, dtype=torch.float32, device=dev)
+        st = int(torch.cuda.current_stream().cuda_stream)
+
+        def step():
+            B.check(L.cf_distances(pa.dev.data_ptr(), pb.dev.data_ptr(), d_pairs.data_ptr(), P, 3.0,
+                                   B.CF_DIST_SCALE01, dout.data_ptr(), dws.data_ptr(), dws.numel(), st))
+        return step, P, 3, tune
+    if name == "optimal":
+        ws_bytes = api.ws_size(pa, pb, pairs_np, B.params(ALPHA, K_ITERS, match_mode=B.CF_MATCH_OPTIMAL))
+        out["X"] = torch.empty(int(x_off[-1]), dtype=torch.float32, device=dev)
+
+        def step():
+            api.similarity(pa, pb, pairs_np, omega, ALPHA, K_ITERS, want_match=True, ws=ws, d_pairs=d_pairs,
+                           out=out, check_status=False, ws_bytes=ws_bytes, tune=tune, optimal=True)
+        return step, P, n_fwd + 1, tune
+    if name == "ward":  # the pair scores are computed once, outside the step
+        api.similarity(pa, pb, pairs_np, omega, ALPHA, K_ITERS, ws=ws, d_pairs=d_pairs, out=out, tune=tune)
+        L = B.lib()
+        n_cfg = len(w.cfgs_a)
+        S = torch.empty(n_cfg, n_cfg, dtype=torch.float32, device=dev)
+        sstat = torch.empty(1, dtype=torch.int32, device=dev)
+        nb = C.c_size_t(0)
+        B.check(L.cf_ward_ws_size(n_cfg, C.byref(nb)))
+        wws = torch.empty(int(nb.value), dtype=torch.uint8, device=dev)
+        merge = torch.empty(n_cfg - 1, 2, dtype=torch.int32, device=dev)
+        height = torch.empty(n_cfg - 1, dtype=torch.float32, device=dev)
+        size = torch.empty(n_cfg - 1, dtype=torch.int32, device=dev)
+        st = int(torch.cuda.current_stream().cuda_stream)
+
+        def step():
+            B.check(L.cf_score_matrix(d_pairs.data_ptr(), out["scores"].data_ptr(), P, n_cfg, n_cfg, 1, S.data_ptr(),
+                                      sstat.data_ptr(), st))
+            B.check(L.cf_ward(S.data_ptr(), n_cfg, n_cfg, merge.data_ptr(), height.data_ptr(), size.data_ptr(),
+                              wws.data_ptr(), wws.numel(), st))
+        return step, 1, 4, tune
     if name in ("cfg2", "cfg3"):
         ws_bytes = api.ws_size(pa, pb, pairs_np, prm)
 
@@ -320,7 +407,8 @@ def make_step(name, dev, tune_cache=None):
 
 
 def run_workload(args):
-    """--workload cfg3 / cfg4 / cfg5: one JSON line for that workload alone."""
+    """--workload cfg3 / cfg4 / cfg5 / dist / optimal / ward: one JSON line for
+    that workload alone (the last three with the oracle timed beside it)."""
     import torch
 
     from paper_1707_02423_gb300 import api
@@ -336,15 +424,21 @@ def run_workload(args):
     if rank != 0:
         return
     mps = tot / args.steps
-    print(json.dumps({
-        "metric": METRIC, "value": job_rate(P, world, mps), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    unit = UNITS.get(args.workload, UNIT)
+    line = {
+        "metric": METRIC, "value": job_rate(P, world, mps), "unit": unit, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "pairs": P,
                    "l2": "flushed between steps (256 MiB write, outside the step events)",
                    "tune": api.tune_info(tune)},
         "gpu_launches": launches * args.steps, "clocks": clk.summary(),
-    }), flush=True)
+    }
+    if args.workload in ("dist", "optimal", "ward"):
+        v, n, dt, what = cpu_next(args.workload, workload(args.workload), args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": unit, "cores": 1, "kind": "oracle",
+                                "sample": f"{what} in {dt:.1f} s"}
+    print(json.dumps(line), flush=True)
 
 
 def run_ours(args):
