@@ -3,7 +3,7 @@ against the FP64 oracle (oracle/distances.py, pinned in
 test_oracle_distances.py).
 
 Bar: every distance within 1e-5 relative plus 1e-6 absolute of the oracle
-(FP32 entries, FP64 accumulation across rows); the [0, 1] scaling within
+(FP32 entries and row sums, compensated sums across rows); the [0, 1] scaling within
 2e-5 absolute."""
 import numpy as np
 import pytest
@@ -80,6 +80,25 @@ def test_edge_cases():
     big = structured_cfg(rng, 700, 6, F - 1)
     cfgs = [one, loop1, empty5, c, big]
     pairs = np.array([(a, b) for a in range(5) for b in range(5)], np.int32)
+    pa = api.Pack(cfgs, F, device=DEV)
+    check(api.distances(pa, pa, pairs, 3.0).cpu().numpy(), OD.run_pairs(cfgs, cfgs, pairs, 3.0))
+
+
+def test_dense_pairs_beyond_the_staged_edge_area():
+    """CFGs small enough for the staged layout, some of whose pairs carry more
+    edges than a warp's staged edge area: those pairs read their CSR from
+    global memory, the others from shared memory, in the same launch."""
+    rng = np.random.default_rng(11)
+    F = 2
+
+    def dense(n, deg):
+        src = np.repeat(np.arange(n), deg).astype(np.int32)
+        dst = np.concatenate([rng.choice(n, deg, replace=False) for _ in range(n)]).astype(np.int32)
+        return CFG(n, src, dst, rng.uniform(0.1, 1.0, n * deg).astype(np.float32),
+                   rng.uniform(0, 1, (n, F)).astype(np.float32))
+
+    cfgs = [dense(100, 5), dense(60, 4), structured_cfg(rng, 30, 3, F - 1), dense(9, 2), dense(2, 2)]
+    pairs = np.array([(a, b) for a in range(len(cfgs)) for b in range(len(cfgs))], np.int32)
     pa = api.Pack(cfgs, F, device=DEV)
     check(api.distances(pa, pa, pairs, 3.0).cpu().numpy(), OD.run_pairs(cfgs, cfgs, pairs, 3.0))
 
