@@ -490,7 +490,7 @@ cf_status cf_similarity(const void* d_pack_a, const void* d_pack_b, const int32_
     if (e != cudaSuccess) return cuda_fail(e, "forward launch");
     if (optimal) {
       if (params->flags & CF_FLAG_REUSE_PLAN) {
-        e = cudaMemsetAsync(static_cast<char*>(d_ws) + offsetof(WsHeader, q_opt), 0, sizeof(uint32_t), st);
+        e = cudaMemsetAsync(static_cast<char*>(d_ws) + offsetof(WsHeader, q_opt), 0, sizeof(uint64_t), st);
         if (e != cudaSuccess) return cuda_fail(e, "queue reset");
       }
       a.X_in = d_X;

@@ -93,6 +93,53 @@ def test_shapes_including_transposed(shape):
     assert abs(value(X.astype(np.float64), m) - s_ref) <= 1e-5
 
 
+def test_many_pairs_both_queue_ends():
+    """A batch large enough that the warps taking pairs from the back of the
+    queue also meet pairs too large for their shared-memory region (those
+    read X from global memory), on near-rank-one matrices like X_K."""
+    from gen import CFG
+
+    rng = np.random.default_rng(5)
+    F = 2
+    sizes = np.concatenate([[1, 2, 31, 32, 33, 64, 65, 96, 97, 127, 128], rng.integers(1, 129, 49)])
+    cfgs = [CFG(int(n), np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.float32),
+                np.ones((int(n), F), np.float32)) for n in sizes]
+    pairs = np.array([(a, b) for a in range(len(cfgs)) for b in range(len(cfgs))], np.int32)
+    pairs = pairs[rng.permutation(len(pairs))[:2500]]
+    mats = []
+    for a, b in pairs:
+        na, nb = int(sizes[a]), int(sizes[b])
+        X = np.outer(rng.uniform(0.5, 1, na), rng.uniform(0.5, 1, nb)) + 0.02 * rng.random((na, nb))
+        mats.append(X.astype(np.float32))
+    pa = api.Pack(cfgs, F, device=DEV)
+    res = api.match(pa, pa, pairs, torch.from_numpy(np.concatenate([m.ravel() for m in mats])).to(DEV), optimal=True)
+    sc, mt = res.scores.cpu().numpy(), res.match.cpu().numpy()
+    for p in range(len(pairs)):
+        X = mats[p].astype(np.float64)
+        m = mt[res.m_off[p]:res.m_off[p + 1]]
+        assert valid_matching(m, *X.shape), p
+        _, s_ref = oracle.optimal_match(X)
+        tol = 1e-5 + 1e-6 * min(X.shape)
+        assert abs(value(X, m) - s_ref) <= tol, (p, X.shape, value(X, m), s_ref)
+        assert abs(float(sc[p]) - value(X, m)) <= tol, p
+
+
+def test_nan_row_sets_numeric_status():
+    from gen import CFG
+
+    from paper_1707_02423_gb300 import _binding as B
+
+    F = 2
+    cfgs = [CFG(n, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.float32),
+                np.ones((n, F), np.float32)) for n in (6, 9)]
+    X = np.random.default_rng(3).random((6, 9)).astype(np.float32)
+    X[4, :] = np.nan
+    pa = api.Pack(cfgs, F, device=DEV)
+    with pytest.raises(B.CfsimError) as e:
+        api.match(pa, pa, [(0, 1)], torch.from_numpy(X.ravel()).to(DEV), optimal=True)
+    assert e.value.status == 6
+
+
 def test_similarity_with_optimal_matching_cfg2_subset():
     w = config2(16)
     pa = api.Pack(w.cfgs_a, w.F, device=DEV)
