@@ -245,8 +245,7 @@ struct WsHeader {
   uint64_t bwd_slot_need;  // bytes of adjoint scratch the largest pair needs
   uint32_t q_bwd;          // adjoint work counter (one-CTA pairs)
   uint32_t q_bwd_big;      // adjoint work counter (pairs on clusters)
-  uint64_t q_opt;          // optimal-matching work counters: pairs taken from the queue's front (low 32 bits)
-                           // and from its back (high 32 bits)
+  uint64_t q_opt;          // optimal-matching work counter (64-bit: claimed by compare-and-swap)
   uint32_t hist[kNumClasses][kBuckets];
   uint32_t cursor[kNumClasses][kBuckets];
   int64_t x_total, m_total;

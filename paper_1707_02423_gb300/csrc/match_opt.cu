@@ -25,12 +25,15 @@
 //  - Larger CFGs: the per-step form with every array in shared memory (the
 //    potentials move by the step's minimum slack at every step).
 //
-// Work distribution (up to 128 columns): a CTA's first warps own large
-// regions that hold the largest pair's X and take pairs from the front of
-// the plan's queue (largest first); the other warps own small regions and
-// take pairs from its back; both ends share one 64-bit counter, so every
-// pair is taken exactly once.  A pair whose X does not fit the warp's region
-// reads X from global memory.
+// Work distribution (up to 128 columns): every warp of a CTA draws its
+// pair's X from a pool of 64 shared-memory slots under one 64-bit mask.
+// Before it takes a pair from the plan's queue (largest pairs first), a
+// warp reserves contiguous slots for the CTA's running estimate of the next
+// pair's size (the size of the last pair a warp of the CTA took), then takes
+// the pair and gives back the slots it does not need.  So no warp holds a
+// pair it cannot stage, and waiting warps watch only the CTA's own mask
+// (shared memory) for a release.  Every wait is bounded: past it a warp
+// takes its pair and reads X from global memory instead.
 #include "device_common.cuh"
 #include "kernels.h"
 
@@ -48,7 +51,7 @@ constexpr int kOptRegCols = 128;  // register form: at most four columns per lan
 // included) and its inverse.
 __device__ __forceinline__ uint32_t ord_key(float f) {
   const uint32_t b = __float_as_uint(f);
-  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+  return b ^ ((uint32_t)((int32_t)b >> 31) | 0x80000000u);
 }
 __device__ __forceinline__ float key_val(uint32_t o) {
   return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
@@ -58,38 +61,44 @@ __device__ __forceinline__ float key_val(uint32_t o) {
 // for up to m_max rows.
 __host__ __device__ __forceinline__ size_t opt_reg_head(int m_max) { return align_up(8 * (size_t)m_max, 16); }
 
-// Bytes of a region that holds the X of any pair of up to m_max blocks a side.
-__host__ __device__ __forceinline__ size_t opt_reg_big(int m_max) {
-  return opt_reg_head(m_max) + align_up(4 * (size_t)m_max * m_max, 16);
-}
+constexpr int kOptSlots = 64;           // shared-memory slots of the X pool (one 64-bit mask)
+constexpr int kOptMaxWaits = 5000;      // polls of the slot mask before staging is given up (>= 10 ms)
 
 // One pair on one warp, S = ceil(max(n_a, n_b) / 32) <= 4 columns per lane.
-// X: n_a x n_b row-major (stride n_b).  Xs: room for the n x m cost rows in
-// shared memory, or NULL to read X from global memory at every step.  u, c4r:
-// n floats / ints of shared memory.  Writes match[n_a] (when mo is not NULL)
-// and the score (every lane); returns false if an insertion found no finite
-// reduced cost (NaN in X).
-template <int S>
+// X: n_a x n_b row-major (stride n_b).  kStaged: Xs holds room for the n x m
+// cost rows in shared memory (else X is read from global memory at every
+// step).  u, c4r: n floats / ints of shared memory.  Writes match[n_a] (when
+// mo is not NULL) and the score (every lane); returns false if an insertion
+// found no finite reduced cost (NaN in X).
+template <int S, bool kStaged>
 __device__ bool assign_regs(const float* __restrict__ X, int n_a, int n_b, float* __restrict__ Xs, float* u, int* c4r,
                             int32_t* mo, float* score) {
   const int lane = threadIdx.x & 31;
   const bool tr = n_a > n_b;  // rows = the smaller side
   const int n = tr ? n_b : n_a, m = tr ? n_a : n_b;
   float xmax = -CUDART_INF_F;
-  if (Xs) {  // stage the n x m cost rows (x values; the cost is formed per step)
-    int i = lane / (m > 0 ? m : 1), k = lane - i * m;
-    for (int d = lane; d < n * m; d += 32) {
-      const float x = __ldg(X + (tr ? (size_t)k * n_b + i : (size_t)i * n_b + k));
-      Xs[d] = x;
-      xmax = fmaxf(xmax, x);
-      k += 32;
-      while (k >= m) {
-        k -= m;
-        ++i;
+  if (kStaged) {
+    // the n x m rows of x (the cost is formed per step): X read in its own
+    // order (coalesced), eight loads in flight per lane, transposed into the
+    // rows of the smaller side where n_a > n_b
+    const int ne = n_a * n_b;
+    for (int e0 = lane; e0 < ne; e0 += 32 * 8) {
+      float xv[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) xv[t] = e0 + 32 * t < ne ? __ldg(X + e0 + 32 * t) : -CUDART_INF_F;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int e = e0 + 32 * t;
+        if (e < ne) {
+          const int ra = e / n_b, cb = e - ra * n_b;  // X(ra, cb)
+          Xs[tr ? cb * m + ra : e] = xv[t];
+          xmax = fmaxf(xmax, xv[t]);
+        }
       }
     }
   } else {
-    for (size_t e = lane; e < (size_t)n_a * n_b; e += 32) xmax = fmaxf(xmax, __ldg(X + e));
+#pragma unroll 8
+    for (int e = lane; e < n_a * n_b; e += 32) xmax = fmaxf(xmax, __ldg(X + e));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
@@ -97,63 +106,60 @@ __device__ bool assign_regs(const float* __restrict__ X, int n_a, int n_b, float
     u[i] = 0.f;
     c4r[i] = -1;
   }
+  // per column slot: potential, owner row, tie bits (owned flag << 16 | column)
   float v[S];
-  int own[S];
+  int own[S], kc[S];
+  uint32_t tb[S];
 #pragma unroll
   for (int j = 0; j < S; ++j) {
     v[j] = 0.f;
     own[j] = -1;
+    tb[j] = (uint32_t)(lane + 32 * j);
+    kc[j] = min(lane + 32 * j, m - 1);  // in-range column for the loads of slots past m
   }
   __syncwarp();
-  auto x_at = [&](int i, int k) -> float {
-    return Xs ? Xs[i * m + k] : __ldg(X + (tr ? (size_t)k * n_b + i : (size_t)i * n_b + k));
-  };
   bool ok = true;
   for (int cur = 0; cur < n; ++cur) {
     float spc[S];
     int path[S];
+    bool live[S];
 #pragma unroll
     for (int j = 0; j < S; ++j) {
       spc[j] = CUDART_INF_F;
       path[j] = -1;
+      live[j] = lane + 32 * j < m;
     }
-    unsigned scanned = 0;
     float min_val = 0.f;
     int i = cur, sink = -1;
     for (int step = 0; step < m; ++step) {  // an insertion scans at most m columns
       const float ui = u[i];
-      uint32_t kb = 0xffffffffu, ki = 0xffffffffu;
+      unsigned long long best = ~0ull;
 #pragma unroll
       for (int j = 0; j < S; ++j) {
-        const int k = lane + 32 * j;
-        if (k < m && !((scanned >> j) & 1u)) {
-          const float r = min_val + ((xmax - x_at(i, k)) - ui - v[j]);
-          if (r < spc[j]) {
-            spc[j] = r;
-            path[j] = i;
-          }
-          const uint32_t a = ord_key(spc[j]);
-          const uint32_t b = (own[j] >= 0 ? 0x10000u : 0u) | (uint32_t)k;
-          if (a < kb || (a == kb && b < ki)) {
-            kb = a;
-            ki = b;
-          }
-        }
+        const float x = kStaged ? Xs[i * m + kc[j]] : __ldg(X + (tr ? (size_t)kc[j] * n_b + i : (size_t)i * n_b + kc[j]));
+        const float r = min_val + ((xmax - x) - ui - v[j]);
+        const bool better = live[j] && r < spc[j];
+        spc[j] = better ? r : spc[j];
+        path[j] = better ? i : path[j];
+        const uint32_t hi = live[j] ? ord_key(spc[j]) : 0xffffffffu;
+        const unsigned long long key = ((unsigned long long)hi << 32) | tb[j];
+        best = key < best ? key : best;
       }
-      const uint32_t wb = __reduce_min_sync(0xffffffffu, kb);
-      const uint32_t wi = __reduce_min_sync(0xffffffffu, kb == wb ? ki : 0xffffffffu);
-      if (wb >= ord_key(CUDART_INF_F)) break;  // no finite reduced cost left: X holds NaN
-      min_val = key_val(wb);
+      const uint32_t bh = (uint32_t)(best >> 32);
+      const uint32_t wh = __reduce_min_sync(0xffffffffu, bh);
+      const uint32_t wi = __reduce_min_sync(0xffffffffu, bh == wh ? (uint32_t)best : 0xffffffffu);
+      if (wh >= ord_key(CUDART_INF_F)) break;  // no finite reduced cost left: X holds NaN
+      min_val = key_val(wh);
       const int ks = (int)(wi & 0xffffu), wl = ks & 31, wj = ks >> 5;
-      if (lane == wl) scanned |= 1u << wj;
+      int o = own[0];
+#pragma unroll
+      for (int j = 1; j < S; ++j) o = wj == j ? own[j] : o;
+#pragma unroll
+      for (int j = 0; j < S; ++j) live[j] = live[j] && !(lane == wl && wj == j);
       if (!(wi & 0x10000u)) {  // a free column: the path ends here
         sink = ks;
         break;
       }
-      int o = -1;
-#pragma unroll
-      for (int j = 0; j < S; ++j)
-        if (j == wj) o = own[j];
       i = __shfl_sync(0xffffffffu, o, wl);
     }
     if (sink < 0) {
@@ -164,7 +170,7 @@ __device__ bool assign_regs(const float* __restrict__ X, int n_a, int n_b, float
     // path's length, and its row (the owners; then the inserted row) to match
 #pragma unroll
     for (int j = 0; j < S; ++j) {
-      if ((scanned >> j) & 1u) {
+      if (lane + 32 * j < m && !live[j]) {
         const float dl = min_val - spc[j];
         v[j] -= dl;
         if (own[j] >= 0) u[own[j]] += dl;
@@ -176,15 +182,18 @@ __device__ bool assign_regs(const float* __restrict__ X, int n_a, int n_b, float
     int j = sink;
     for (int hop = 0; hop <= n; ++hop) {
       const int jl = j & 31, jj = j >> 5;
-      int pi = -1;
+      int pi = path[0];
 #pragma unroll
-      for (int t = 0; t < S; ++t)
-        if (t == jj) pi = path[t];
+      for (int t = 1; t < S; ++t) pi = jj == t ? path[t] : pi;
       pi = __shfl_sync(0xffffffffu, pi, jl);
       if (lane == jl) {
 #pragma unroll
-        for (int t = 0; t < S; ++t)
-          if (t == jj) own[t] = pi;
+        for (int t = 0; t < S; ++t) {
+          if (t == jj) {
+            own[t] = pi;
+            tb[t] = 0x10000u | (uint32_t)(lane + 32 * t);
+          }
+        }
       }
       const int prev = c4r[pi];
       __syncwarp();
@@ -354,14 +363,10 @@ __device__ __forceinline__ int pack_max_blocks(const void* pack) {
   return reinterpret_cast<const PackHeader*>(pack)->max_blocks;
 }
 
-// Takes the next queue position from the front (or the back); -1 once the
-// two ends have met.  One atomic on the 64-bit pair of counts orders every
-// take, so a position is taken once.
-__device__ __forceinline__ int take_pair(unsigned long long* ctr, bool front, uint32_t n_pairs) {
-  const unsigned long long old = atomicAdd(ctr, front ? 1ull : (1ull << 32));
-  const uint32_t f = (uint32_t)old, b = (uint32_t)(old >> 32);
-  if ((uint64_t)f + b >= n_pairs) return -1;
-  return front ? (int)f : (int)(n_pairs - 1 - b);
+// Takes the next queue position; -1 once the queue is drained.
+__device__ __forceinline__ int take_pair(unsigned long long* ctr, uint32_t n_pairs) {
+  const unsigned long long old = atomicAdd(ctr, 1ull);
+  return old < n_pairs ? (int)old : -1;
 }
 
 // Status and score of one finished pair.
@@ -370,6 +375,45 @@ __device__ __forceinline__ void finish_pair(const CallArgs& a, WsHeader* hdr, in
     if (!ok) set_status(hdr, 6 /* CF_ERR_NUMERIC */, p);
     if (a.scores) a.scores[p] = sc;
   }
+}
+
+// First of k contiguous free slots in mask m; -1 if no run of k is free.
+__device__ __forceinline__ int first_run(unsigned long long m, int k) {
+  const unsigned long long fr = ~m;
+  unsigned long long r = fr;  // bit s: slots s .. s + k - 1 all free
+  for (int i = 1; i < k && r; ++i) r &= fr >> i;
+  return r ? __ffsll((long long)r) - 1 : -1;
+}
+
+__device__ __forceinline__ unsigned long long run_bits(int s, int k) {
+  return (k >= 64 ? ~0ull : ((1ull << k) - 1)) << s;
+}
+
+// Frees what wait_slots took, after the warp's last use of the slots.
+__device__ __forceinline__ void release_slots(unsigned long long* mask, int s, int k) {
+  __threadfence_block();
+  atomicAnd(mask, ~run_bits(s, k));
+}
+
+// Takes k contiguous slots, waiting while other warps of the CTA hold them:
+// a warp sleeps only while the mask still holds the very value in which it
+// found no free run, so a release cannot go unseen.  -1 after kOptMaxWaits
+// polls (or if k can never fit).
+__device__ __forceinline__ int wait_slots(unsigned long long* mask, int k) {
+  if (k <= 0 || k > kOptSlots) return -1;
+  for (int polls = 0; polls < kOptMaxWaits; ++polls) {
+    const unsigned long long m = *reinterpret_cast<volatile unsigned long long*>(mask);
+    const int s = first_run(m, k);
+    if (s >= 0) {
+      if (atomicCAS(mask, m, m | run_bits(s, k)) == m) return s;
+      continue;  // the mask moved under us: look again at once
+    }
+    while (polls < kOptMaxWaits && *reinterpret_cast<volatile unsigned long long*>(mask) == m) {
+      __nanosleep(4000);  // long sleeps: waiting warps must not take issue slots from working ones
+      ++polls;
+    }
+  }
+  return -1;
 }
 
 __global__ void __launch_bounds__(kOptNT) match_optimal_kernel(CallArgs a) {
@@ -386,52 +430,73 @@ __global__ void __launch_bounds__(kOptNT) match_optimal_kernel(CallArgs a) {
   uint32_t n_pairs = 0;
   for (int c = 0; c < kNumClasses; ++c) n_pairs += hdr->n_class[c];
   if (m_max <= kOptRegCols) {
-    // warps [0, n_big): regions that hold any pair's X, front of the queue;
-    // the others: equal shares of the rest, back of the queue
-    const size_t bb = opt_reg_big(m_max);
-    const int n_big = max(1, min(4, (int)(kOptSmem * 11 / 20 / bb)));
-    const size_t bs = ((kOptSmem - (size_t)n_big * bb) / (kOptNT / 32 - n_big)) & ~(size_t)15;
-    const bool big = w < n_big;
-    unsigned char* region = big ? smem + (size_t)w * bb : smem + (size_t)n_big * bb + (size_t)(w - n_big) * bs;
+    // per warp: u and the row-to-column map; then the X pool, kOptSlots
+    // slots of `slot` bytes
+    __shared__ unsigned long long s_mask;
+    __shared__ int s_kest;
     const size_t head = opt_reg_head(m_max);
-    const size_t cap = ((big ? bb : bs) - head) / sizeof(float);
-    float* u = reinterpret_cast<float*>(region);
+    const size_t slot = ((kOptSmem - (kOptNT / 32) * head) / kOptSlots) & ~(size_t)15;
+    if (threadIdx.x == 0) {
+      s_mask = 0ull;
+      s_kest = (int)((4 * (size_t)m_max * m_max + slot - 1) / slot);
+    }
+    __syncthreads();
+    unsigned char* pool = smem + (kOptNT / 32) * head;
+    float* u = reinterpret_cast<float*>(smem + (size_t)w * head);
     int* c4r = reinterpret_cast<int*>(u + m_max);
-    float* xs = reinterpret_cast<float*>(region + head);
     for (;;) {
-      int q = 0;
-      if (lane == 0) q = take_pair(ctr, big, n_pairs);
+      int q = -1, s0 = -1, k = 0;
+      if (lane == 0) {
+        // reserve room for the estimate, take a pair, keep what it needs
+        const int k_est = *reinterpret_cast<volatile int*>(&s_kest);
+        int r0 = wait_slots(&s_mask, k_est);
+        q = take_pair(ctr, n_pairs);
+        if (q >= 0) {
+          const int p = (int)queue[q];
+          const int pa = a.pairs[2 * p], pb = a.pairs[2 * p + 1];
+          const size_t bytes = 4 * (size_t)(A.node_off[pa + 1] - A.node_off[pa]) *
+                               (size_t)(B.node_off[pb + 1] - B.node_off[pb]);
+          k = (int)((bytes + slot - 1) / slot);
+          s_kest = k > 0 ? k : 1;
+          if (r0 >= 0 && k <= k_est) {
+            if (k < k_est) release_slots(&s_mask, r0 + k, k_est - k);
+            s0 = k > 0 ? r0 : -1;
+          } else {
+            if (r0 >= 0) release_slots(&s_mask, r0, k_est);
+            s0 = k > 0 ? wait_slots(&s_mask, k) : -1;
+          }
+        } else if (r0 >= 0) {
+          release_slots(&s_mask, r0, k_est);
+        }
+      }
       q = __shfl_sync(0xffffffffu, q, 0);
       if (q < 0) break;
+      s0 = __shfl_sync(0xffffffffu, s0, 0);
+      k = __shfl_sync(0xffffffffu, k, 0);
       const int p = (int)queue[q];
       const int pa = a.pairs[2 * p], pb = a.pairs[2 * p + 1];
       const int na = A.node_off[pa + 1] - A.node_off[pa];
       const int nb = B.node_off[pb + 1] - B.node_off[pb];
-      float* Xs = (size_t)na * nb <= cap ? xs : nullptr;
+      float* Xs = s0 >= 0 ? reinterpret_cast<float*>(pool + (size_t)s0 * slot) : nullptr;
       const float* X = a.X_in + x_off[p];
       int32_t* mo = a.match ? a.match + m_off[p] : nullptr;
       float sc = 0.f;
-      bool ok;
-      switch ((max(na, nb) + 31) >> 5) {
-        case 0:
-        case 1: ok = assign_regs<1>(X, na, nb, Xs, u, c4r, mo, &sc); break;
-        case 2: ok = assign_regs<2>(X, na, nb, Xs, u, c4r, mo, &sc); break;
-        case 3: ok = assign_regs<3>(X, na, nb, Xs, u, c4r, mo, &sc); break;
-        default: ok = assign_regs<4>(X, na, nb, Xs, u, c4r, mo, &sc); break;
-      }
+      const bool ok = Xs ? assign_regs<4, true>(X, na, nb, Xs, u, c4r, mo, &sc)
+                         : assign_regs<4, false>(X, na, nb, Xs, u, c4r, mo, &sc);
+      if (lane == 0 && s0 >= 0) release_slots(&s_mask, s0, k);  // assign_regs ends in a warp barrier
       finish_pair(a, hdr, p, ok, sc);
     }
     return;
   }
   // larger CFGs: the per-step form, regions sized for the larger pack's
-  // largest CFG (capped at opt_cap()), front of the queue only
+  // largest CFG (capped at opt_cap())
   int warps = (int)(kOptSmem / opt_warp_bytes(m_max));
   warps = warps > kOptNT / 32 ? kOptNT / 32 : warps;
   if (w >= warps) return;
   unsigned char* region = smem + (size_t)w * opt_warp_bytes(m_max);
   for (;;) {
     int q = 0;
-    if (lane == 0) q = take_pair(ctr, true, n_pairs);
+    if (lane == 0) q = take_pair(ctr, n_pairs);
     q = __shfl_sync(0xffffffffu, q, 0);
     if (q < 0) break;
     const int p = (int)queue[q];
