@@ -300,15 +300,17 @@ __global__ void __launch_bounds__(kDistNT) distances_kernel(const void* pack_a, 
   }
 }
 
-// Min-max scaling of each distance over the call's pairs (one CTA).
-__global__ void __launch_bounds__(1024) distances_scale_kernel(int P, float* out, const DistWs* ws) {
+// Min-max scaling of each distance over the call's pairs (grid-stride over
+// the P x 5 values).
+__global__ void __launch_bounds__(256) distances_scale_kernel(int P, float* out, const DistWs* ws) {
   __shared__ float lo[kNumDist], span[kNumDist];
   if (threadIdx.x < kNumDist) {
     lo[threadIdx.x] = __uint_as_float(ws->lo[threadIdx.x]);
     span[threadIdx.x] = __uint_as_float(ws->hi[threadIdx.x]) - lo[threadIdx.x];
   }
   __syncthreads();
-  for (size_t e = threadIdx.x; e < (size_t)P * kNumDist; e += blockDim.x) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)P * kNumDist;
+       e += (size_t)gridDim.x * blockDim.x) {
     const int k = (int)(e % kNumDist);
     out[e] = span[k] > 0.f ? (out[e] - lo[k]) / span[k] : 0.f;
   }
@@ -353,7 +355,10 @@ cudaError_t launch_distances(const void* pack_a, const void* pack_b, const int32
   distances_init_kernel<<<1, 32, 0, s>>>(w);
   const int g = P < grid ? P : grid;
   if (g > 0) distances_kernel<<<g, kDistNT, kDistSmem, s>>>(pack_a, pack_b, pairs, P, p, out, w);
-  if (scale && P > 0) distances_scale_kernel<<<1, 1024, 0, s>>>(P, out, w);
+  if (scale && P > 0) {
+    const size_t blocks = ((size_t)P * kNumDist + 255) / 256;
+    distances_scale_kernel<<<(unsigned)(blocks < (size_t)grid ? blocks : (size_t)grid), 256, 0, s>>>(P, out, w);
+  }
   return cudaGetLastError();
 }
 
