@@ -93,10 +93,11 @@ def test_shapes_including_transposed(shape):
     assert abs(value(X.astype(np.float64), m) - s_ref) <= 1e-5
 
 
-def test_many_pairs_both_queue_ends():
-    """A batch large enough that the warps taking pairs from the back of the
-    queue also meet pairs too large for their shared-memory region (those
-    read X from global memory), on near-rank-one matrices like X_K."""
+def test_many_pairs_through_the_slot_pool():
+    """A batch large enough that every CTA's shared-memory slot pool fills,
+    fragments and turns over many times, with pairs of every width up to 128
+    blocks (the register form's limit, including 32/33, 64/65, 96/97 and
+    127/128), on near-rank-one matrices like X_K."""
     from gen import CFG
 
     rng = np.random.default_rng(5)
