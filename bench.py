@@ -17,7 +17,7 @@ from __future__ import annotations
 import os
 
 for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-    os.environ.setdefault(_v, "1")  # the CPU oracle runs single-threaded (cores = 1)
+    os.environ.setdefault(_v, "1")  # each oracle process runs one thread (cores = processes)
 
 import argparse  # noqa: E402
 import hashlib  # noqa: E402
@@ -153,24 +153,80 @@ def profiled_traffic(kernel_src: str):
     return None
 
 
-def cpu_oracle(w, seconds: float, seed: int = 0):
-    """The FP64 oracle as it stands, single-threaded, on a seeded random
-    sample of the workload's pairs, until `seconds` have elapsed."""
+def host_cores() -> int:
+    """Host cores this process may run on (the oracle's process count), at most 32."""
+    try:
+        n = len(os.sched_getaffinity(0))
+    except AttributeError:
+        n = os.cpu_count() or 1
+    return max(1, min(32, n))
+
+
+_POOL_WORKLOAD = None
+
+
+def _pool_init(name):
+    global _POOL_WORKLOAD
+    _POOL_WORKLOAD = workload(name)
+
+
+def _pool_pairs(idx):
     import oracle
 
-    rng = np.random.default_rng(seed)
-    order = rng.permutation(len(w.pairs))
+    w = _POOL_WORKLOAD
     om = np.ones(w.F)
-    t0 = time.perf_counter()
-    done = 0
-    for p in order:
+    for p in idx:
         a, b = w.pairs[p]
         oracle.pair_score(w.cfgs_a[a], w.cfgs_b[b], om, ALPHA, K_ITERS)
-        done += 1
-        if time.perf_counter() - t0 >= seconds and done >= 20:
-            break
-    dt = time.perf_counter() - t0
-    return done / dt, done, dt
+    return len(idx)
+
+
+class OraclePool:
+    """The FP64 oracle as it stands on `cores` worker processes, one thread
+    each, over independent pairs (the per-pair arithmetic is unchanged).  The
+    workers are spawned, not forked, so a pool started after CUDA
+    initialisation is safe."""
+
+    def __init__(self, name: str, cores: int):
+        import multiprocessing as mp
+
+        self.cores = cores
+        self.pool = mp.get_context("spawn").Pool(cores, initializer=_pool_init, initargs=(name,))
+
+    def run(self, idx, chunk: int = 2) -> int:
+        idx = [int(i) for i in idx]
+        parts = [idx[i:i + chunk] for i in range(0, len(idx), chunk)]
+        return sum(self.pool.map(_pool_pairs, parts, chunksize=1))
+
+    def rate(self, idx) -> float:
+        """Pairs per second over idx (workers already started)."""
+        t0 = time.perf_counter()
+        n = self.run(idx)
+        return n / (time.perf_counter() - t0)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_oracle(w, seconds: float, seed: int = 0, name: str = "cfg2"):
+    """The oracle on all host cores, on a seeded random sample of the
+    workload's pairs sized for about `seconds` of work (at most every pair):
+    (pairs/s, pairs timed, seconds, cores)."""
+    cores = host_cores()
+    order = np.random.default_rng(seed).permutation(len(w.pairs))
+    pool = OraclePool(name, cores)
+    try:
+        pool.run(order[:2 * cores])  # starts every worker (spawn + imports), untimed
+        est = pool.rate(order[2 * cores:4 * cores])
+        n = int(min(len(order) - 4 * cores, max(4 * cores, est * seconds)))
+        sample = order[4 * cores:4 * cores + n]
+        t0 = time.perf_counter()
+        done = pool.run(sample)
+        dt = time.perf_counter() - t0
+    finally:
+        pool.close()
+    return done / dt, done, dt, cores
 
 
 def cpu_next(name, w, seconds: float):
@@ -245,45 +301,38 @@ def job_rate(pairs_per_rank: int, world: int, ms_per_step: float) -> float:
 
 
 def run_reference(args):
-    """The reference arm: the FP64 CPU oracle, timed on the host cores."""
+    """The reference arm: the FP64 CPU oracle on all host cores."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     w = workload()
-    import oracle
-
-    om = np.ones(w.F)
-    rng = np.random.default_rng(1)
-    order = rng.permutation(len(w.pairs))
-    # size each step so that warmup + steps take about 90 s on this host
-    t0 = time.perf_counter()
-    for p in order[:10]:
-        a, b = w.pairs[p]
-        oracle.pair_score(w.cfgs_a[a], w.cfgs_b[b], om, ALPHA, K_ITERS)
-    t_pair = (time.perf_counter() - t0) / 10
-    per_step = int(min(300, max(3, 90.0 / ((args.steps + args.warmup) * t_pair))))
-    sample = order[:per_step]
-
-    def step():
-        for p in sample:
-            a, b = w.pairs[p]
-            oracle.pair_score(w.cfgs_a[a], w.cfgs_b[b], om, ALPHA, K_ITERS)
-
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    dt = time.perf_counter() - t0
+    cores = host_cores()
+    order = np.random.default_rng(1).permutation(len(w.pairs))
+    pool = OraclePool("cfg2", cores)
+    try:
+        pool.run(order[:2 * cores])  # starts every worker (spawn + imports), untimed
+        est = pool.rate(order[2 * cores:4 * cores])
+        # size each step so that warmup + steps take about args.ref_seconds
+        per_step = int(min(len(order), max(2 * cores, args.ref_seconds * est / (args.steps + args.warmup))))
+        sample = order[:per_step]
+        for _ in range(args.warmup):
+            pool.run(sample)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            pool.run(sample)
+        dt = time.perf_counter() - t0
+    finally:
+        pool.close()
     v = len(sample) * args.steps / dt
-    desc = f"{per_step} seeded random pairs of the workload per step, single-threaded FP64 oracle (numpy/scipy)"
+    desc = (f"{per_step} seeded random pairs of the workload per step, FP64 oracle (numpy/scipy) on {cores} "
+            "processes of one thread each")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "reference": "FP64 CPU oracle (oracle/isorank.py), host cores"},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -580,7 +629,7 @@ def run_ours(args):
     peaks = measured_peaks()
     hbm_bytes = int(pack.host.size + pairs_np.nbytes + P * 4 + m_elems * 4)
     traffic = profiled_traffic(os.path.join(ROOT, "paper_1707_02423_gb300", "csrc", "forward.cu"))
-    cpu_v, cpu_n, cpu_dt = cpu_oracle(w, args.cpu_seconds)
+    cpu_v, cpu_n, cpu_dt, cpu_cores = cpu_oracle(w, args.cpu_seconds)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -607,9 +656,9 @@ def run_ours(args):
                     "workload": WORKLOADS["cfg4"]},
         "per_pair": {"value": P / (pp_ms * 1e-3), "unit": UNIT, "ms_per_step": pp_ms, "launches_per_step": P,
                      "speedup_batched_over_per_pair": pp_ms / ms_per_step},
-        "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{cpu_n} seeded random pairs of the workload in {cpu_dt:.1f} s, "
-                                   "single-threaded FP64 oracle (numpy/scipy)"},
+        "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cpu_cores, "kind": "oracle",
+                         "sample": f"{cpu_n} seeded random pairs of the workload in {cpu_dt:.1f} s, FP64 oracle "
+                                   f"(numpy/scipy) on {cpu_cores} processes of one thread each"},
         "e2e": {"value": world * P / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_s * 1e3,
                 "what": "cf_pack_cfgs (host build + copy) + pinned pair upload + cf_similarity + pinned "
@@ -630,6 +679,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=90.0,
+                    help="--impl reference: oracle work per run (warmup + steps), in seconds")
     ap.add_argument("--workload", default="cfg2", choices=sorted(WORKLOADS))
     ap.add_argument("--tune-cache", default=os.environ.get("CF_AUTOTUNE_CACHE") or
                     os.path.join(tempfile.gettempdir(), "cfsim_autotune.cache"))
