@@ -283,6 +283,9 @@ cf_status cf_ward(const float* d_points, int32_t n, int32_t dim, int32_t* d_merg
  *     not fit in 32 MiB is rejected with CF_ERR_WORKSPACE before any launch;
  *     pairs too large for shared memory need scratch slots from the rest of
  *     the array, and *d_status is CF_ERR_WORKSPACE if none fits.
+ *   - params->flags may not hold CF_FLAG_PLAN_ONLY or CF_FLAG_REUSE_PLAN
+ *     (CF_ERR_INVALID_ARG): every call plans afresh, because a plan kept in
+ *     the shared array can be replaced by any other call in between.
  *   - All calls share the array; each call clears what must start at zero.
  *     Calls whose device work can overlap (other streams without ordering)
  *     race on the array and give wrong results.

@@ -24,6 +24,7 @@
 
 #include "../../include/cfsim.h"
 #include "device_common.cuh"
+#include "device_state.h"
 #include "kernels.h"
 
 namespace cfsim {
@@ -340,17 +341,17 @@ int dist_max_blocks() {
 
 cudaError_t launch_distances(const void* pack_a, const void* pack_b, const int32_t* pairs, int P, float p, bool scale,
                              float* out, void* ws, cudaStream_t s) {
-  static bool init = false;
-  static int grid = 0;
-  if (!init) {
-    cudaError_t e = cudaFuncSetAttribute(distances_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDistSmem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, n_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    grid = n_sm;
-    init = true;
-  }
+  static DeviceOnce once;
+  static int grids[kMaxDevices];
+  int dev = 0;
+  const cudaError_t ie = once.run(
+      [](int d) {
+        grids[d] = sm_count_of(d);
+        return cudaFuncSetAttribute(distances_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDistSmem);
+      },
+      &dev);
+  if (ie != cudaSuccess) return ie;
+  const int grid = grids[dev];
   DistWs* w = static_cast<DistWs*>(ws);
   distances_init_kernel<<<1, 32, 0, s>>>(w);
   const int g = P < grid ? P : grid;

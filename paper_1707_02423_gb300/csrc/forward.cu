@@ -31,6 +31,7 @@
 // per-row edge ranges and {u * ld, w} entries, so a gather is two dependent
 // shared loads and the lanes sharing a row read the same words.
 #include "device_common.cuh"
+#include "device_state.h"
 #include "kernels.h"
 
 namespace cfsim {
@@ -1390,58 +1391,51 @@ __global__ void __launch_bounds__(kMatchNT) match_only_kernel(CallArgs a) {
   }
 }
 
-int g_n_sm = 0;
-
+// Per device: the kernel's shared-memory limit and the SM count (the grid).
 template <int NT>
-cudaError_t fwd_init() {
-  static bool done = false;
-  if (done) return cudaSuccess;
-  cudaError_t e =
-      cudaFuncSetAttribute(fwd_batched_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
-  if (e != cudaSuccess) return e;
-  int dev = 0, n = 0;
-  e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return e;
-  g_n_sm = n;
-  done = true;
-  return cudaSuccess;
+cudaError_t fwd_init(int* n_sm) {
+  static DeviceOnce once;
+  static int sms[kMaxDevices];
+  int dev = 0;
+  const cudaError_t e = once.run(
+      [](int d) {
+        const cudaError_t r =
+            cudaFuncSetAttribute(fwd_batched_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+        sms[d] = sm_count_of(d);
+        return r != cudaSuccess ? r : (sms[d] > 0 ? cudaSuccess : cudaErrorInvalidDevice);
+      },
+      &dev);
+  *n_sm = e == cudaSuccess ? sms[dev] : 0;
+  return e;
 }
 
 template <int NT>
 cudaError_t launch_fwd(const CallArgs& a, bool per_pair, cudaStream_t s) {
-  cudaError_t e = fwd_init<NT>();
+  int n_sm = 0;
+  cudaError_t e = fwd_init<NT>(&n_sm);
   if (e != cudaSuccess) return e;
   if (per_pair) {
     for (int p = 0; p < a.P; ++p) fwd_batched_kernel<NT><<<1, NT, kFwdSmem, s>>>(a, p);
   } else {
-    fwd_batched_kernel<NT><<<g_n_sm, NT, kFwdSmem, s>>>(a, -1);
+    fwd_batched_kernel<NT><<<n_sm, NT, kFwdSmem, s>>>(a, -1);
   }
   return cudaGetLastError();
 }
 
-template <int NT>
-struct ClusterInit {
-  bool done = false;
-  int n_clusters[kMaxCluster + 1] = {};  // resident clusters per size, -1 unknown
-};
-
-template <int NT>
-ClusterInit<NT>& cluster_init() {
-  static ClusterInit<NT> ci;
-  if (!ci.done) {
-    for (int c = 0; c <= kMaxCluster; ++c) ci.n_clusters[c] = -1;
-    ci.done = true;
-  }
-  return ci;
-}
-
+// Resident clusters of C CTAs of fwd_cluster_kernel<NT>, per device and C
+// (queried once each; 0 if none fit).
 template <int NT>
 int resident_clusters(int C) {
-  ClusterInit<NT>& ci = cluster_init<NT>();
+  static std::mutex mu;
+  static int known[kMaxDevices][kMaxCluster + 1];  // 0 unknown, else 1 + the count
   if (C < 2 || C > kMaxCluster) return 0;
-  if (ci.n_clusters[C] >= 0) return ci.n_clusters[C];
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return 0;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (known[dev][C] > 0) return known[dev][C] - 1;
   int n = 0;
   if (cudaFuncSetAttribute(fwd_cluster_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem) ==
           cudaSuccess &&
@@ -1460,7 +1454,7 @@ int resident_clusters(int C) {
     if (cudaOccupancyMaxActiveClusters(&n, fwd_cluster_kernel<NT>, &cfg) != cudaSuccess) n = 0;
   }
   cudaGetLastError();
-  ci.n_clusters[C] = n;
+  known[dev][C] = 1 + n;
   return n;
 }
 
@@ -1517,19 +1511,18 @@ cudaError_t launch_forward(const CallArgs& a, int variant, bool per_pair, cudaSt
 }
 
 cudaError_t launch_match_only(const CallArgs& a, cudaStream_t s) {
-  static bool init = false;
-  static int grid = 0;
+  static DeviceOnce once;
+  static int grid[kMaxDevices];
   const size_t sm = 2 * (3 * (size_t)kMaxBlocks + 16);
-  if (!init) {
-    cudaError_t e = cudaFuncSetAttribute(match_only_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    int dev = 0, n_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    grid = n_sm;
-    init = true;
-  }
-  const int g = a.P < grid ? a.P : grid;
+  int dev = 0;
+  const cudaError_t e = once.run(
+      [sm](int d) {
+        grid[d] = sm_count_of(d);
+        return cudaFuncSetAttribute(match_only_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      },
+      &dev);
+  if (e != cudaSuccess) return e;
+  const int g = a.P < grid[dev] ? a.P : grid[dev];
   if (g > 0) match_only_kernel<<<g, kMatchNT, sm, s>>>(a);
   return cudaGetLastError();
 }

@@ -35,6 +35,7 @@
 // (shared memory) for a release.  Every wait is bounded: past it a warp
 // takes its pair and reads X from global memory instead.
 #include "device_common.cuh"
+#include "device_state.h"
 #include "kernels.h"
 
 namespace cfsim {
@@ -519,17 +520,17 @@ __global__ void __launch_bounds__(kOptNT) match_optimal_kernel(CallArgs a) {
 int opt_max_blocks() { return opt_cap(); }
 
 cudaError_t launch_match_optimal(const CallArgs& a, cudaStream_t s) {
-  static bool init = false;
-  static int grid = 0;
-  if (!init) {
-    cudaError_t e = cudaFuncSetAttribute(match_optimal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOptSmem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, n_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    grid = n_sm;
-    init = true;
-  }
+  static DeviceOnce once;
+  static int grids[kMaxDevices];
+  int dev = 0;
+  const cudaError_t ie = once.run(
+      [](int d) {
+        grids[d] = sm_count_of(d);
+        return cudaFuncSetAttribute(match_optimal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOptSmem);
+      },
+      &dev);
+  if (ie != cudaSuccess) return ie;
+  const int grid = grids[dev];
   const int g = a.P < grid ? a.P : grid;
   if (g > 0) match_optimal_kernel<<<g, kOptNT, kOptSmem, s>>>(a);
   return cudaGetLastError();

@@ -17,6 +17,9 @@
 //     call clears the part that must start at zero (the workspace header) on
 //     its stream.  Calls whose device work overlaps (different streams, no
 //     ordering between them) race on the array and give wrong results.
+//   - CF_FLAG_PLAN_ONLY and CF_FLAG_REUSE_PLAN are rejected with
+//     CF_ERR_INVALID_ARG: a plan left in the shared array by one call is not
+//     safe for a later one.
 //   - The first call on a device resolves the array's device address with
 //     cudaGetSymbolAddress (that device current).  Make that first call before
 //     any stream capture begins.
@@ -75,6 +78,16 @@ extern "C" cf_status cf_similarity_noalloc(const void* d_pack_a, const void* d_p
                                            int32_t P, const cf_params* params, const float* d_omega, float* d_X,
                                            float* d_scores, int32_t* d_match, int32_t* d_status,
                                            cf_stream_t stream) {
+  // The plan flags would let a call run on a plan an earlier call left in the
+  // shared array; any other call in between (another pair list, another user
+  // of the library) replaces that plan, and offsets sized for other pairs
+  // could then write outside this caller's outputs.  Every call plans afresh.
+  if (params && (params->flags & (CF_FLAG_PLAN_ONLY | CF_FLAG_REUSE_PLAN))) {
+    cfsim::set_error_detail(
+        "cf_similarity_noalloc: CF_FLAG_PLAN_ONLY and CF_FLAG_REUSE_PLAN are not accepted (the static workspace "
+        "is shared by every call, so a kept plan cannot be relied on)");
+    return CF_ERR_INVALID_ARG;
+  }
   if (P > 0 && cfsim::ws_layout(P).fixed_bytes > kStaticWsBytes) {
     cfsim::set_error_detail(
         "cf_similarity_noalloc: the pair list needs more workspace than the 32 MiB static array holds; "

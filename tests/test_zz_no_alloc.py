@@ -78,3 +78,22 @@ def test_noalloc_rejects_pair_lists_beyond_its_limit():
                                 omega.data_ptr(), None, None, None, None, None)
     assert s == 2  # CF_ERR_WORKSPACE
     assert b"32 MiB" in L.cf_last_error_detail()
+
+
+@pytest.mark.parametrize("flag", ["plan_only", "reuse_plan"])
+def test_noalloc_rejects_plan_flags(flag):
+    """A plan kept in the shared array could belong to another call's pairs,
+    so the flags that keep or reuse a plan are refused before any launch."""
+    w = config1()
+    pack = api.Pack(w.cfgs_a, w.F, device=DEV)
+    L = B.lib()
+    prm = B.params(flags=B.CF_FLAG_PLAN_ONLY if flag == "plan_only" else B.CF_FLAG_REUSE_PLAN)
+    omega = torch.ones(w.F, device=DEV)
+    d_pairs = torch.from_numpy(np.ascontiguousarray(w.pairs, np.int32)).to(DEV)
+    sc = torch.full((len(w.pairs),), -7.0, device=DEV)
+    s = L.cf_similarity_noalloc(pack.dev.data_ptr(), pack.dev.data_ptr(), d_pairs.data_ptr(), len(w.pairs),
+                                C.byref(prm), omega.data_ptr(), None, sc.data_ptr(), None, None, None)
+    assert s == 1  # CF_ERR_INVALID_ARG
+    assert b"REUSE_PLAN" in L.cf_last_error_detail()
+    torch.cuda.synchronize()
+    assert float(sc.min()) == -7.0  # nothing ran
