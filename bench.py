@@ -356,7 +356,7 @@ def timed_steps(step, steps, warmup, flush, stream):
     return [e0.elapsed_time(e1) for e0, e1 in ev]
 
 
-def make_step(name, dev, tune_cache=None):
+def make_step(name, dev, tune_cache=None, bwd_tune=0):
     """The step of one workload through the Python API (kernel configuration
     from the autotuner): returns (step, n_pairs, launches_per_step, tune)."""
     import ctypes as C
@@ -435,12 +435,19 @@ def make_step(name, dev, tune_cache=None):
         ws_bytes = api.ws_size(pa, pb, pairs_np, prm)
         bws = api.Workspace(dev)
         g = torch.ones(P, dtype=torch.float32, device=dev)
+        grads = {"grad_w_a": torch.zeros(int(pa.info.n_user_edges), dtype=torch.float32, device=dev),
+                 "grad_omega": torch.zeros(w.F, dtype=torch.float32, device=dev)}
+        if not w.shared:
+            grads["grad_w_b"] = torch.zeros(int(pb.info.n_user_edges), dtype=torch.float32, device=dev)
 
         def step():
             api.similarity(pa, pb, pairs_np, omega, ALPHA, K_ITERS, want_match=True, ws=ws, d_pairs=d_pairs,
                            out=out, check_status=False, ws_bytes=ws_bytes, tune=tune)
-            api.similarity_backward(pa, pb, pairs_np, omega, out["match"], g, ALPHA, K_ITERS, ws=bws)
-        return step, P, n_fwd + n_bwd, tune
+            for t in grads.values():  # the caller's accumulators start at zero every step
+                t.zero_()
+            api.similarity_backward(pa, pb, pairs_np, omega, out["match"], g, ALPHA, K_ITERS, ws=bws, out=grads,
+                                    d_pairs=d_pairs, check_status=False, tune=bwd_tune)
+        return step, P, n_fwd + n_bwd + len(grads), tune
     # cfg5: scores of every query-corpus pair, top-16 per query, matchings of the winners
     nq, nc, k = w.meta["n_query"], w.meta["n_corpus"], w.meta["top_k"]
     ws_bytes = api.ws_size(pa, pb, pairs_np, prm)

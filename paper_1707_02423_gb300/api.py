@@ -298,30 +298,47 @@ def backward_ws_size(pa: Pack, pb: Pack, pairs_np: np.ndarray, prm: B.cf_params)
 
 def similarity_backward(pa: Pack, pb: Pack, pairs, omega: torch.Tensor, match: torch.Tensor,
                         grad_scores: torch.Tensor, alpha: float = 0.8, K: int = 40, *,
-                        norm_mode: int = B.CF_NORM_FROB, ws: Workspace | None = None, stream=None):
+                        norm_mode: int = B.CF_NORM_FROB, ws: Workspace | None = None, stream=None,
+                        tune: int = 0, check_status: bool = True, out: dict | None = None,
+                        d_pairs: torch.Tensor | None = None):
     """Gradients of sum_p grad_scores[p] * s_p (cf_similarity_backward) with the
     matching ``match`` (from the forward) held fixed.
 
     Returns ``(grad_w_a, grad_w_b, grad_omega)``: user-edge-order gradients of
     pack A's and pack B's edge weights (``grad_w_b`` is None when both sides
-    are the same pack: everything is in ``grad_w_a``) and of omega."""
+    are the same pack: everything is in ``grad_w_a``) and of omega.
+
+    ``tune`` selects the adjoint's kernel configuration (0: its default;
+    otherwise a tune id's thread count and cluster size).  ``out`` may hold
+    zeroed ``grad_w_a`` / ``grad_w_b`` / ``grad_omega`` tensors to accumulate
+    into (for CUDA-graph capture, with ``d_pairs``, a sized ``ws`` and
+    ``check_status=False``)."""
     L = B.lib()
     pairs_np = _pairs_np(pairs)
     P = len(pairs_np)
     dev = pa.dev.device
-    prm = B.params(alpha, K, norm_mode)
-    gwa = torch.zeros(int(pa.info.n_user_edges), dtype=torch.float32, device=dev)
-    gwb = None if pb is pa else torch.zeros(int(pb.info.n_user_edges), dtype=torch.float32, device=dev)
-    gom = torch.zeros(pa.F, dtype=torch.float32, device=dev)
+    prm = B.params(alpha, K, norm_mode, tune=tune)
+    out = {} if out is None else out
+    gwa = out.get("grad_w_a")
+    if gwa is None:
+        gwa = torch.zeros(int(pa.info.n_user_edges), dtype=torch.float32, device=dev)
+    gwb = None if pb is pa else out.get("grad_w_b")
+    if gwb is None and pb is not pa:
+        gwb = torch.zeros(int(pb.info.n_user_edges), dtype=torch.float32, device=dev)
+    gom = out.get("grad_omega")
+    if gom is None:
+        gom = torch.zeros(pa.F, dtype=torch.float32, device=dev)
     ws = ws or Workspace(dev)
     wbuf = ws.get(backward_ws_size(pa, pb, pairs_np, prm))
-    d_pairs = torch.from_numpy(pairs_np).to(dev)
+    if d_pairs is None:
+        d_pairs = torch.from_numpy(pairs_np).to(dev)
     g = grad_scores.detach().to(torch.float32).contiguous()
     st = _stream_ptr(stream)
     B.check(L.cf_similarity_backward(pa.dev.data_ptr(), pb.dev.data_ptr(), d_pairs.data_ptr(), P, C.byref(prm),
                                      omega.detach().contiguous().data_ptr(), match.data_ptr(), g.data_ptr(),
                                      gwa.data_ptr(), _ptr(gwb), gom.data_ptr(), wbuf.data_ptr(), wbuf.numel(), st))
-    B.check(L.cf_status_check(wbuf.data_ptr(), st))
+    if check_status:
+        B.check(L.cf_status_check(wbuf.data_ptr(), st))
     return gwa, gwb, gom
 
 

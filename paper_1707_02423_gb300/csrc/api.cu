@@ -312,6 +312,23 @@ Tune decode_tune(int32_t id) {
 
 namespace {
 
+// Kernel configuration of the adjoint: tune 0 is its default (512 threads,
+// clusters of kBwdDefaultCluster CTAs for the pairs that fit no single CTA:
+// the fastest measured on the 256-pair gradient workload); another tune id
+// gives its thread count (1024 runs as 768, which the adjoint is built for)
+// and cluster size.
+constexpr int kBwdDefaultCluster = 8;
+void bwd_config(const cf_params* p, int* variant, int* cluster) {
+  if (!p || p->tune == 0) {
+    *variant = 1;
+    *cluster = kBwdDefaultCluster;
+    return;
+  }
+  const Tune t = decode_tune(p->tune);
+  *variant = t.variant == 1 ? 1 : 2;
+  *cluster = t.cluster;
+}
+
 CallArgs base_args(const void* d_pack_a, const void* d_pack_b, const int32_t* d_pairs, int32_t P,
                    const cf_params* params, const float* d_omega, void* d_ws, size_t ws_bytes) {
   CallArgs a{};
@@ -542,20 +559,36 @@ cf_status cf_similarity_backward_ws_size(const void* h_pack_a, const void* h_pac
   if (s) return s;
   s = scan_pairs(h_pack_a, h_pack_b, h_pairs, P, nullptr, nullptr, nullptr, nullptr);
   if (s) return s;
+  int variant = 0, cluster = 0;
+  bwd_config(params, &variant, &cluster);
+  const BwdShape sh = bwd_shape(variant, cluster, params->K);
+  if (sh.n_cta <= 0) return fail(CF_ERR_CUDA, "cf_similarity_backward_ws_size: no usable CUDA device");
   const int32_t* noa = reinterpret_cast<const int32_t*>(static_cast<const char*>(h_pack_a) + ha.off_node);
   const int32_t* nob = reinterpret_cast<const int32_t*>(static_cast<const char*>(h_pack_b) + hb.off_node);
   const int32_t* eoa = reinterpret_cast<const int32_t*>(static_cast<const char*>(h_pack_a) + ha.off_edge);
   const int32_t* eob = reinterpret_cast<const int32_t*>(static_cast<const char*>(h_pack_b) + hb.off_edge);
+  const uint8_t* xda = reinterpret_cast<const uint8_t*>(static_cast<const char*>(h_pack_a) + ha.off_xdeg);
+  const uint8_t* xdb = reinterpret_cast<const uint8_t*>(static_cast<const char*>(h_pack_b) + hb.off_xdeg);
+  // the classification of the device-side plan: pairs that fit no single CTA
+  // need a team slot (the largest such pair sizes them)
   size_t need = 0;
+  int64_t n_big = 0;
   for (int p = 0; p < P; ++p) {
     const int a = h_pairs[2 * p], b = h_pairs[2 * p + 1];
-    need = std::max(need, bwd_slot_bytes(noa[a + 1] - noa[a], nob[b + 1] - nob[b], eoa[a + 1] - eoa[a],
-                                         eob[b + 1] - eob[b], params->K, ha.F_pad));
+    const int na = noa[a + 1] - noa[a], nb = nob[b + 1] - nob[b];
+    const int ea = eoa[a + 1] - eoa[a], eb = eob[b + 1] - eob[b];
+    const Shape sp = classify(na, nb, ea, eb, sh.cc, xda[a], xdb[b]);
+    if (sp.cls == kClassGlobal) {
+      need = std::max(need, bwd_slot_bytes(na, nb, ea, eb, params->K, ha.F_pad));
+      ++n_big;
+    } else if (sp.cls == kClassCluster) {
+      need = std::max(need, bwd_res_slot_bytes(sp.n_row, sp.ld, params->K));
+      ++n_big;
+    }
   }
-  const int sms = device_sm_count();
-  const int64_t slots = std::min<int64_t>(P, 2 * (sms > 0 ? sms : 152));
+  const int64_t slots = std::min<int64_t>(n_big, sh.n_teams);
   // sized as if the two sides were different packs (covers both cases)
-  *bytes = bwd_layout(P, ha.n_edges, hb.n_edges, false).slots + (size_t)slots * need;
+  *bytes = bwd_layout(P, ha.n_edges, hb.n_edges, false).slots + (size_t)sh.n_cta * sh.area_bytes + (size_t)slots * need;
   return ok();
 }
 
@@ -573,18 +606,23 @@ cf_status cf_similarity_backward(const void* d_pack_a, const void* d_pack_b, con
   if (d_pack_a == d_pack_b && d_grad_w_b && d_grad_w_b != d_grad_w_a)
     return fail(CF_ERR_INVALID_ARG, "with one pack on both sides, d_grad_w_b must be NULL or equal d_grad_w_a");
   if (P == 0) return ok();
+  int variant = 0, cluster = 0;
+  bwd_config(params, &variant, &cluster);
+  const BwdShape sh = bwd_shape(variant, cluster, params->K);
+  if (sh.n_cta <= 0) return fail(CF_ERR_CUDA, "cf_similarity_backward: no usable CUDA device");
   CallArgs a = base_args(d_pack_a, d_pack_b, d_pairs, P, params, d_omega, d_ws, ws_bytes);
   a.match_in = d_match;
   a.grad_scores = d_grad_scores;
   a.grad_w_a = d_grad_w_a;
   a.grad_w_b = d_pack_a == d_pack_b ? nullptr : d_grad_w_b;
   a.grad_omega = d_grad_omega;
+  a.cluster = sh.cluster;
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaMemsetAsync(d_ws, 0, sizeof(WsHeader), st);
   if (e != cudaSuccess) return cuda_fail(e, "workspace reset");
-  e = launch_plan(a, fwd_class_cfg(0, a.min_cls, a.ranked, 0), st);
+  e = launch_plan(a, sh.cc, st);
   if (e != cudaSuccess) return cuda_fail(e, "plan launch");
-  e = launch_backward(a, st);
+  e = launch_backward(a, variant, st);
   if (e != cudaSuccess) return cuda_fail(e, "backward launch");
   return ok();
 }

@@ -71,8 +71,20 @@ int opt_max_blocks();
 cudaError_t launch_set_weights(CfAdj* out_adj, CfAdj* in_adj, const int32_t* in_eid, const int32_t* u2c,
                                int64_t n_user_edges, int64_t n_edges, const float* w_user, cudaStream_t s);
 
-// a8: adjoint (workspace layout bwd_layout; the plan must have run).
-cudaError_t launch_backward(const CallArgs& a, cudaStream_t s);
+// a8: adjoint (workspace layout bwd_layout, then the per-CTA slot areas of
+// the resident tier, then the per-team slots of the cluster and global tiers;
+// the plan must have run with the adjoint's class configuration bwd_shape().cc).
+// variant: 1 = 512 threads per CTA, else 768; a.cluster: CTAs per cluster of
+// the cluster tier (0 none), as bwd_shape() reported it.
+struct BwdShape {
+  int cluster;        // CTAs per cluster actually launched (0: none)
+  int n_cta;          // CTAs of the launch (one slot area each)
+  int n_teams;        // teams that run cluster- or global-class pairs (one slot each at most)
+  size_t area_bytes;  // slot area per CTA
+  ClassCfg cc;        // classification of the pairs
+};
+BwdShape bwd_shape(int variant, int cluster, int K);
+cudaError_t launch_backward(const CallArgs& a, int variant, cudaStream_t s);
 
 // The element-wise Table 1 distances of resized transition matrices
 // (workspace dist_ws_bytes(); CFGs up to dist_max_blocks() blocks).

@@ -82,6 +82,7 @@ struct ClassCfg {
                 // state fits, 1 only in groups of at most a quarter CTA,
                 // 2 never (rescans)
   int cluster;  // CTAs per cluster of the cluster tier (0: no cluster tier)
+  int bwd;      // 1: size regions for the adjoint (bwd_resident_bytes), 0: the forward
 };
 
 // How a pair maps onto a group of G threads.  The "row" graph indexes the
@@ -106,11 +107,23 @@ CF_HD size_t resident_bytes(int n_row, int ld, int e_row, int n_col, int e_col) 
          align_up(8 * (size_t)(n_col + 1), 16) + align_up(8 + 4 * (size_t)n_row, 16);
 }
 
-CF_HD bool fits(int n_row, int n_col, int e_row, int e_col, int G, size_t region, int* R, int* M) {
+// The adjoint keeps the same three matrices (the iterate being gathered, the
+// next one or the adjoint being gathered, and a third), the same staged lists,
+// and per edge of either graph its source ({row byte offset} or {column byte
+// offset}, int32) and its gradient accumulator (float): 8 more bytes per edge.
+CF_HD size_t bwd_resident_bytes(int n_row, int ld, int e_row, int n_col, int e_col) {
+  return resident_bytes(n_row, ld, e_row, n_col, e_col) + align_up(8 * (size_t)(e_row + e_col), 16);
+}
+
+CF_HD size_t pair_bytes(int n_row, int ld, int e_row, int n_col, int e_col, int bwd) {
+  return bwd ? bwd_resident_bytes(n_row, ld, e_row, n_col, e_col) : resident_bytes(n_row, ld, e_row, n_col, e_col);
+}
+
+CF_HD bool fits(int n_row, int n_col, int e_row, int e_col, int G, size_t region, int* R, int* M, int bwd = 0) {
   if (n_col > G) return false;
   *R = G / n_col;
   *M = ceil_div(n_row, *R);
-  return resident_bytes(n_row, pair_ld(n_col), e_row, n_col, e_col) <= region;
+  return pair_bytes(n_row, pair_ld(n_col), e_row, n_col, e_col, bwd) <= region;
 }
 
 CF_HD int group_size(int cls, const ClassCfg& c) {
@@ -149,8 +162,8 @@ CF_HD Shape classify(int na, int nb, int ea, int eb, const ClassCfg& c, int xa =
     const int G = group_size(cls, c);
     const size_t Z = group_region(cls, c);
     int R0 = 0, M0 = 0, R1 = 0, M1 = 0;
-    const bool f0 = fits(na, nb, ea, eb, G, Z, &R0, &M0);
-    const bool f1 = fits(nb, na, eb, ea, G, Z, &R1, &M1);
+    const bool f0 = fits(na, nb, ea, eb, G, Z, &R0, &M0, c.bwd);
+    const bool f1 = fits(nb, na, eb, ea, G, Z, &R1, &M1, c.bwd);
     if (f0 || f1) {
       const bool tr = !f0 || (f1 && prefer_tr(M0, M1, xa, xb));
       s.cls = cls;
@@ -168,8 +181,8 @@ CF_HD Shape classify(int na, int nb, int ea, int eb, const ClassCfg& c, int xa =
     // three matrices, its slab's row lists and the whole column graph
     int M0 = 0, M1 = 0;
     const int s0 = ceil_div(na, c.cluster), s1 = ceil_div(nb, c.cluster);
-    const bool f0 = nb <= c.nt && resident_bytes(s0, pair_ld(nb), ea, nb, eb) <= (size_t)c.z_cta;
-    const bool f1 = na <= c.nt && resident_bytes(s1, pair_ld(na), eb, na, ea) <= (size_t)c.z_cta;
+    const bool f0 = nb <= c.nt && pair_bytes(s0, pair_ld(nb), ea, nb, eb, c.bwd) <= (size_t)c.z_cta;
+    const bool f1 = na <= c.nt && pair_bytes(s1, pair_ld(na), eb, na, ea, c.bwd) <= (size_t)c.z_cta;
     if (f0) M0 = ceil_div(s0, c.nt / nb);
     if (f1) M1 = ceil_div(s1, c.nt / na);
     if (f0 || f1) {
@@ -223,6 +236,31 @@ CF_HD size_t bwd_slot_bytes(int na, int nb, int ea, int eb, int K, int Fp) {
   return align_up(4 * floats, kAlign);
 }
 
+// Matrices of n_row x ld floats in the global (L2-resident) slot of a pair
+// whose adjoint runs resident in shared memory: the checkpoints Y_0, Y_S, ...
+// (K / S + 1), one segment of iterates (indices 1 .. S-1 of the segment; the
+// last segment's Y_K lands at index K mod S), Ehat, the Ehat adjoint, and a
+// stash of the X adjoint while a segment is recomputed.  Before them, the
+// norms |Y_k|, k = 0 .. K, rounded up to 64 floats.
+CF_HD int bwd_res_mats(int K) { return K / bwd_segment(K) + 1 + bwd_segment(K) + 3; }
+CF_HD size_t bwd_res_norm_floats(int K) { return align_up((size_t)K + 2, 64); }
+CF_HD size_t bwd_res_slot_bytes(int n_row, int ld, int K) {
+  return align_up(4 * (bwd_res_norm_floats(K) + (size_t)n_row * ld * bwd_res_mats(K)), kAlign);
+}
+
+// Global-slot bytes per shared-memory byte of a group's region, in 1/256
+// units: any pair a region of Z bytes holds has n_row ld <= Z / 12 (three
+// matrices), so a slot of Z ratio / 256 bytes (less one alignment unit)
+// holds its matrices and norms whenever Z >= z_min, the smallest region.
+CF_HD uint64_t bwd_slot_ratio_q(int K, size_t z_min) {
+  const uint64_t per_entry = 4 * (uint64_t)bwd_res_mats(K);  // bytes per entry
+  const uint64_t fixed = 4 * bwd_res_norm_floats(K) + 4 * (uint64_t)bwd_res_mats(K) + 2 * kAlign;
+  return (256 * per_entry + 11) / 12 + (256 * fixed + z_min - 1) / z_min + 1;
+}
+// Byte offset of the slot of a group whose region starts at byte ro of its
+// CTA's shared memory, within that CTA's slot area.
+CF_HD size_t bwd_slot_at(size_t ro, uint64_t ratio_q) { return align_up((size_t)(ro * ratio_q / 256), kAlign); }
+
 // Cost bucket: two buckets per octave of the per-iteration work.
 CF_HD int cost_bucket(int64_t cost) {
   int b = 0;
@@ -246,6 +284,7 @@ struct WsHeader {
   uint32_t q_bwd;          // adjoint work counter (one-CTA pairs)
   uint32_t q_bwd_big;      // adjoint work counter (pairs on clusters)
   uint64_t q_opt;          // optimal-matching work counter (64-bit: claimed by compare-and-swap)
+  uint64_t bwd_big_need;   // adjoint scratch bytes of the largest cluster- or global-class pair
   uint32_t hist[kNumClasses][kBuckets];
   uint32_t cursor[kNumClasses][kBuckets];
   int64_t x_total, m_total;

@@ -46,6 +46,7 @@ struct PairFacts {
   bool valid;
   int na, nb, ea, eb;
   int cls, bucket;
+  int n_row, ld;  // resident matrix shape (classify)
 };
 
 __device__ __forceinline__ PairFacts pair_facts(const PlanCtx& c, int p, const ClassCfg& cc) {
@@ -64,6 +65,8 @@ __device__ __forceinline__ PairFacts pair_facts(const PlanCtx& c, int p, const C
   f.eb = eb;
   Shape s = classify(f.na, f.nb, ea, eb, cc, __ldg(c.A.xdeg + pa), __ldg(c.B.xdeg + pb));
   f.cls = s.cls;
+  f.n_row = s.n_row;
+  f.ld = s.ld;
   // per-iteration work: every entry is written once, every edge pair gathered twice
   f.bucket = cost_bucket((int64_t)f.na * f.nb + 2 * (int64_t)ea * eb);
   return f;
@@ -120,6 +123,13 @@ __global__ void __launch_bounds__(kPlanThreads) plan_count_kernel(CallArgs a, Cl
                   (unsigned long long)global_slot_bytes(f.na, f.nb));
       atomicMax(reinterpret_cast<unsigned long long*>(&c.hdr->bwd_slot_need),
                 (unsigned long long)bwd_slot_bytes(f.na, f.nb, f.ea, f.eb, a.K, c.A.F_pad));
+      // the adjoint's per-team slots of pairs not resident in one CTA: the
+      // full-matrix layout of the cluster tier, or the global tier's own
+      if (cc.bwd && (f.cls == kClassGlobal || f.cls == kClassCluster))
+        atomicMax(reinterpret_cast<unsigned long long*>(&c.hdr->bwd_big_need),
+                  (unsigned long long)(f.cls == kClassCluster ? bwd_res_slot_bytes(f.n_row, f.ld, a.K)
+                                                              : bwd_slot_bytes(f.na, f.nb, f.ea, f.eb, a.K,
+                                                                               c.A.F_pad)));
       xc = (int64_t)f.na * f.nb;
       mc = f.na;
     }

@@ -38,20 +38,26 @@ def check_close(got, ref, what):
     got = np.asarray(got, np.float64)
     scale = np.abs(ref).max()
     assert scale > 0, what
-    assert np.abs(got - ref).max() <= REL * scale, (what, np.abs(got - ref).max(), scale)
+    err = np.abs(got - ref)
+    assert err.max() <= REL * scale, (what, err.max(), scale)
     big = np.abs(ref) >= 0.01 * scale
-    rel = np.abs(got[big] - ref[big]) / np.abs(ref[big])
+    rel = err[big] / np.abs(ref[big])
     assert rel.max() <= REL, (what, rel.max())  # per-element, on entries >= 1% of max
+    # every element: relative 1e-4, or absolute 1e-6 of the largest (FP32 sums of many terms)
+    assert (err <= np.maximum(REL * np.abs(ref), 1e-6 * scale)).all(), (
+        what, float((err / np.maximum(np.abs(ref), 1e-30)).max()), float(err.max() / scale))
+    return float(err.max() / scale)
 
 
-def grad_parity(cfgs_a, cfgs_b, pairs, F, omega, alpha=0.8, K=40, norm_mode=0, seed=0, margin=1e-5):
+def grad_parity(cfgs_a, cfgs_b, pairs, F, omega, alpha=0.8, K=40, norm_mode=0, seed=0, margin=1e-5, tune=0,
+                g_all=None):
     shared = cfgs_b is cfgs_a
     pa = api.Pack(cfgs_a, F, device=DEV)
     pb = pa if shared else api.Pack(cfgs_b, F, device=DEV)
     om = torch.tensor(omega, dtype=torch.float32, device=DEV)
     res = api.similarity(pa, pb, pairs, om, alpha, K, want_match=True, norm_mode=norm_mode)
     rng = np.random.default_rng(seed)
-    g = rng.uniform(0.5, 1.5, len(pairs))
+    g = rng.uniform(0.5, 1.5, len(pairs)) if g_all is None else np.full(len(pairs), float(g_all))
     n_used = 0
     ua, ub = user_offsets(cfgs_a), user_offsets(cfgs_b)
     ref_a = np.zeros(ua[-1])
@@ -74,7 +80,7 @@ def grad_parity(cfgs_a, cfgs_b, pairs, F, omega, alpha=0.8, K=40, norm_mode=0, s
     assert n_used >= max(1, len(pairs) // 3), n_used
     gwa, gwb, gom = api.similarity_backward(pa, pb, pairs, om, res.match,
                                             torch.tensor(g, dtype=torch.float32, device=DEV), alpha, K,
-                                            norm_mode=norm_mode)
+                                            norm_mode=norm_mode, tune=tune)
     check_close(gwa.cpu().numpy(), ref_a, "grad_w_a")
     if not shared:
         check_close(gwb.cpu().numpy(), ref_b, "grad_w_b")
@@ -142,3 +148,29 @@ def test_autograd_function_matches_oracle():
         ref_o += og["grad_omega"]
     check_close(w_a.grad.cpu().numpy(), ref_a, "autograd w")
     check_close(om.grad.cpu().numpy(), ref_o, "autograd omega")
+
+
+def _largest_and_smallest(w, n_big, n_small):
+    n = np.array([c.n for c in w.cfgs_a])
+    size = n[w.pairs[:, 0]] * n[w.pairs[:, 1]]
+    order = np.argsort(size)
+    return w.pairs[np.concatenate([order[-n_big:], order[:n_small]])]
+
+
+# The adjoint's kernel configurations by tune id (threads per CTA, cluster
+# size of the tier for pairs that fit no single CTA): 768/512 threads with no
+# cluster tier (those pairs run on one CTA out of L2 slots), then clusters of
+# 2, 4 and 8 CTAs (the largest pairs fit only 8-CTA clusters; under 2 and 4
+# they too take the L2 tier, now on a whole cluster).
+@pytest.mark.parametrize("tune", [3, 2, 48, 93, 92, 138])
+def test_tiers_by_tune(tune):
+    w = config4()
+    pairs = _largest_and_smallest(w, 6, 6)
+    grad_parity(w.cfgs_a, w.cfgs_a, pairs, w.F, np.linspace(0.7, 1.3, w.F), seed=5, tune=tune)
+
+
+def test_cfg4_full_workload():
+    """All 256 pairs of the 256-pair gradient workload (n 10-300) in the
+    configuration bench.py times (the default), upstream gradient 1 as there."""
+    w = config4()
+    grad_parity(w.cfgs_a, w.cfgs_a, w.pairs, w.F, np.ones(w.F), g_all=1.0)
