@@ -85,6 +85,111 @@ def algorithmic(w, K):
     return onchip, flops, int(nn.sum()), int(n[a].sum())
 
 
+def algorithmic_bwd(w, K):
+    """Algorithmic on-chip bytes of one adjoint call (cf_similarity_backward)
+    over the workload's pairs, by the same rule as the forward: every operand
+    a step needs read once, every result written once, 4 bytes each.
+
+    Per pair (n_a n_b entries, e_a e_b successor pairs and as many
+    predecessor pairs), with S = ceil(sqrt K) and R = (S - 1) * (number of
+    segments but the last) recomputed steps:
+      forward step (the first pass and each recomputed one):
+        4 (2 e_a e_b + 2 n_a n_b)  -- gathered entries, (1-alpha) Ehat, Y written
+      adjoint step (K of them):
+        4 (2 e_a e_b + 2 n_a n_b)  -- Zbar gathered, Xbar written, Y_k read for <Xbar, X_k>
+      + 4 (4 n_a n_b)              -- Ybar pass: Xbar, Y_{k+1} read; Zbar, Y_k written
+      + 4 (4 e_a e_b)              -- edge terms: Zbar and Y_k at both ends of each pair of edges
+    Returns (bytes, flops) with flops = 2 per gathered pair and edge term."""
+    n = np.array([c.n for c in w.cfgs_a], np.int64)
+    e = np.array([len(set(zip(c.src.tolist(), c.dst.tolist()))) for c in w.cfgs_a], np.int64)
+    a, b = w.pairs[:, 0], w.pairs[:, 1]
+    nn = n[a] * n[b]
+    ee = e[a] * e[b]
+    S = 1
+    while S * S < K:
+        S += 1
+    nseg = (K - 1) // S + 1 if K > 0 else 0
+    R = (S - 1) * max(nseg - 1, 0)
+    fwd_step = 4 * (2 * ee + 2 * nn)
+    adj_step = 4 * (2 * ee + 2 * nn) + 4 * 4 * nn + 4 * 4 * ee
+    onchip = int(((K + R) * fwd_step + K * adj_step).sum())
+    flops = int(((K + R) * (4 * ee + 5 * nn) + K * (4 * ee + 3 * nn + 6 * ee)).sum())
+    return onchip, flops
+
+
+def fwd_bwd_measure(dev, tune_cache, steps=5, warmup=3, bwd_tune=0):
+    """The gradient workload: forward (scores + matchings) then the adjoint,
+    each timed with CUDA events on the launching stream, L2 flushed before
+    every step."""
+    import torch
+
+    from paper_1707_02423_gb300 import api
+
+    w = workload("cfg4")
+    fwd, bwd, P, tune = make_fwd_bwd(w, dev, tune_cache, bwd_tune)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(warmup):
+        flush.zero_()
+        fwd()
+        bwd()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    for e in ev:
+        flush.zero_()
+        e[0].record(stream)
+        fwd()
+        e[1].record(stream)
+        bwd()
+        e[2].record(stream)
+    torch.cuda.synchronize()
+    step_ms = float(np.mean([e[0].elapsed_time(e[2]) for e in ev]))
+    fwd_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
+    bwd_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
+    onchip, flops = algorithmic_bwd(w, K_ITERS)
+    return {"P": P, "step_ms": step_ms, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "bwd_bytes": onchip,
+            "bwd_flops": flops, "tune": api.tune_info(tune)}
+
+
+def make_fwd_bwd(w, dev, tune_cache=None, bwd_tune=0):
+    """(forward, adjoint, P, tune) callables of the gradient workload through
+    the Python API, every buffer allocated up front."""
+    import torch
+
+    from paper_1707_02423_gb300 import _binding as B
+    from paper_1707_02423_gb300 import api
+
+    pairs_np = np.ascontiguousarray(w.pairs, np.int32)
+    P = len(pairs_np)
+    pa = api.Pack(w.cfgs_a, w.F, device=dev)
+    pb = pa if w.shared else api.Pack(w.cfgs_b, w.F, device=dev)
+    omega = torch.ones(w.F, dtype=torch.float32, device=dev)
+    d_pairs = torch.from_numpy(pairs_np).to(dev)
+    ws, bws = api.Workspace(dev), api.Workspace(dev)
+    prm = B.params(ALPHA, K_ITERS)
+    x_off, m_off = api.out_offsets(pa, pb, pairs_np)
+    out = {"scores": torch.empty(P, dtype=torch.float32, device=dev),
+           "match": torch.empty(int(m_off[-1]), dtype=torch.int32, device=dev)}
+    tune, _ = api.autotune(pa, pb, pairs_np, omega, ALPHA, K_ITERS, cache_path=tune_cache)
+    ws_bytes = api.ws_size(pa, pb, pairs_np, prm)
+    g = torch.ones(P, dtype=torch.float32, device=dev)
+    grads = {"grad_w_a": torch.zeros(int(pa.info.n_user_edges), dtype=torch.float32, device=dev),
+             "grad_omega": torch.zeros(w.F, dtype=torch.float32, device=dev)}
+    if not w.shared:
+        grads["grad_w_b"] = torch.zeros(int(pb.info.n_user_edges), dtype=torch.float32, device=dev)
+
+    def fwd():
+        api.similarity(pa, pb, pairs_np, omega, ALPHA, K_ITERS, want_match=True, ws=ws, d_pairs=d_pairs,
+                       out=out, check_status=False, ws_bytes=ws_bytes, tune=tune)
+
+    def bwd():
+        for t in grads.values():  # the caller's accumulators start at zero every step
+            t.zero_()
+        api.similarity_backward(pa, pb, pairs_np, omega, out["match"], g, ALPHA, K_ITERS, ws=bws, out=grads,
+                                d_pairs=d_pairs, check_status=False, tune=bwd_tune)
+    return fwd, bwd, P, tune
+
+
 class ClockSampler:
     """nvidia-smi samples (200 ms) while the timed region runs."""
 
@@ -383,7 +488,7 @@ def make_step(name, dev, tune_cache=None, bwd_tune=0):
     # and, under a cluster tune, the cluster-tier kernel; per adjoint call: the
     # three plan kernels, the accumulator reset, the adjoint and the scatter
     n_fwd = 4 + (1 if api.tune_info(tune)["cluster"] >= 2 else 0)
-    n_bwd = 3 + 1 + 1 + (1 if w.shared else 2)
+    n_bwd = 3 + 1 + 2 + (1 if w.shared else 2)  # plan, zero, large-pair and resident kernels, scatter
     if name == "dist":  # the C ABI directly, every buffer allocated before the timed region
         L = B.lib()
         n = C.c_size_t(0)
@@ -432,22 +537,12 @@ def make_step(name, dev, tune_cache=None, bwd_tune=0):
                            out=out, check_status=False, ws_bytes=ws_bytes, tune=tune)
         return step, P, n_fwd, tune
     if name == "cfg4":
-        ws_bytes = api.ws_size(pa, pb, pairs_np, prm)
-        bws = api.Workspace(dev)
-        g = torch.ones(P, dtype=torch.float32, device=dev)
-        grads = {"grad_w_a": torch.zeros(int(pa.info.n_user_edges), dtype=torch.float32, device=dev),
-                 "grad_omega": torch.zeros(w.F, dtype=torch.float32, device=dev)}
-        if not w.shared:
-            grads["grad_w_b"] = torch.zeros(int(pb.info.n_user_edges), dtype=torch.float32, device=dev)
+        fwd, bwd, _, tune = make_fwd_bwd(w, dev, tune_cache, bwd_tune)
 
         def step():
-            api.similarity(pa, pb, pairs_np, omega, ALPHA, K_ITERS, want_match=True, ws=ws, d_pairs=d_pairs,
-                           out=out, check_status=False, ws_bytes=ws_bytes, tune=tune)
-            for t in grads.values():  # the caller's accumulators start at zero every step
-                t.zero_()
-            api.similarity_backward(pa, pb, pairs_np, omega, out["match"], g, ALPHA, K_ITERS, ws=bws, out=grads,
-                                    d_pairs=d_pairs, check_status=False, tune=bwd_tune)
-        return step, P, n_fwd + n_bwd + len(grads), tune
+            fwd()
+            bwd()
+        return step, P, n_fwd + n_bwd + (2 if w.shared else 3), tune
     # cfg5: scores of every query-corpus pair, top-16 per query, matchings of the winners
     nq, nc, k = w.meta["n_query"], w.meta["n_corpus"], w.meta["top_k"]
     ws_bytes = api.ws_size(pa, pb, pairs_np, prm)
@@ -588,9 +683,9 @@ def run_ours(args):
     pp_ms = e0.elapsed_time(e1) / pp_steps
 
     # ---- forward + adjoint on the gradient workload (256 pairs, n 10-300)
-    fb_step, fb_p, _, _ = make_step("cfg4", dev, args.tune_cache)
-    fb_ms = timed_steps(fb_step, 5, 3, flush, stream)
-    fb_mps = float(np.mean(fb_ms))
+    fb = fwd_bwd_measure(dev, args.tune_cache)
+    fb_mps = fb["step_ms"]
+    fb_p = fb["P"]
 
     # ---- end to end through the C ABI with host buffers: build + upload the
     # pack from the host CFG arrays, upload the pairs from pinned memory,
@@ -665,7 +760,15 @@ def run_ours(args):
                              "frac": (hbm_bytes / (ms_per_step * 1e-3) / 1e9) / peaks["hbm_gbs"]
                              if peaks.get("hbm_gbs") else None, "peak_source": "MEASURED_PEAKS.json (of measured)"}},
         "fwd_bwd": {"value": fb_p / (fb_mps * 1e-3), "unit": UNIT, "ms_per_step": fb_mps,
-                    "workload": WORKLOADS["cfg4"]},
+                    "workload": WORKLOADS["cfg4"], "fwd_ms": fb["fwd_ms"], "bwd_ms": fb["bwd_ms"],
+                    "roofline": {"bound": "smem", "kernel": "bwd_big_kernel + bwd_res_kernel (concurrent, the "
+                                 "whole adjoint call)",
+                                 "achieved": fb["bwd_bytes"] / (fb["bwd_ms"] * 1e-3) / 1e9,
+                                 "peak": smem_peak_gbs, "unit": "GB/s",
+                                 "frac": fb["bwd_bytes"] / (fb["bwd_ms"] * 1e-3) / 1e9 / smem_peak_gbs,
+                                 "traffic": None, "algorithmic_bytes_per_launch": fb["bwd_bytes"],
+                                 "flops_per_launch": fb["bwd_flops"], "kernel_ms": fb["bwd_ms"],
+                                 "peak_source": "of measured: the same shared-memory peak as the forward's line"}},
         "per_pair": {"value": P / (pp_ms * 1e-3), "unit": UNIT, "ms_per_step": pp_ms, "launches_per_step": P,
                      "speedup_batched_over_per_pair": pp_ms / ms_per_step},
         "cpu_baseline": cpu_baseline,
