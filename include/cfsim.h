@@ -83,8 +83,12 @@ enum {
                                         form the batched path is measured against           */
   CF_FLAG_PLAN_ONLY = 1u << 1,       /* run only the device-side plan of the pair list (cost
                                         order, offsets) into the workspace                  */
-  CF_FLAG_REUSE_PLAN = 1u << 2       /* skip the plan: reuse the one a previous call with the
+  CF_FLAG_REUSE_PLAN = 1u << 2,      /* skip the plan: reuse the one a previous call with the
                                         same packs, pairs and workspace left there          */
+  CF_FLAG_OPT_UNSTAGED = 1u << 3     /* testing: under CF_MATCH_OPTIMAL every matrix is read
+                                        from global memory instead of being staged in the
+                                        kernel's shared-memory slot pool -- the path a warp
+                                        takes when its bounded wait for slots runs out       */
 };
 
 typedef struct cf_params {
@@ -215,6 +219,24 @@ cf_status cf_similarity_backward(const void* d_pack_a, const void* d_pack_b, con
  * 1 <= k <= C, k <= 1024. */
 cf_status cf_topk(const float* d_scores, int32_t Q, int32_t C, int32_t k, float* d_top, int32_t* d_idx,
                   cf_stream_t stream);
+
+/* The winners' pair list of a top-k, on the device, so that their matchings
+ * can follow the top-k in the same stream (and the same CUDA graph) without a
+ * host round trip: for query q < Q and rank r < k,
+ *   d_pairs[2 (q k + r)]     = d_rows ? d_rows[q] : q   (the query's CFG in pack A)
+ *   d_pairs[2 (q k + r) + 1] = d_idx[q k + r]           (the winner's CFG in pack B)
+ * d_idx: int32 [Q, k] (cf_topk's indices); d_rows: int32 [Q] or NULL; d_pairs:
+ * int32 [Q k, 2], caller-owned.  Size the matching call's workspace with
+ * cf_similarity_ws_size_any (the pairs are not on the host). */
+cf_status cf_topk_pairs(const int32_t* d_idx, int32_t Q, int32_t k, const int32_t* d_rows, int32_t* d_pairs,
+                        cf_stream_t stream);
+
+/* Workspace bytes cf_similarity / cf_match need for ANY list of P pairs of
+ * these two packs (host copies): an upper bound of cf_similarity_ws_size for
+ * pair lists that exist only on the device (e.g. from cf_topk_pairs).  It
+ * sizes every pair as the two packs' largest CFGs. */
+cf_status cf_similarity_ws_size_any(const void* h_pack_a, const void* h_pack_b, int32_t P, const cf_params* params,
+                                    size_t* bytes);
 
 /* ---- the element-wise distances of Table 1 --------------------------------- */
 /* The paper's other family of measures (Sec. 4, 4.1, Table 1): the smaller

@@ -18,6 +18,7 @@ CF_MATCH_OPTIMAL = 1
 CF_FLAG_PER_PAIR_LAUNCH = 1
 CF_FLAG_PLAN_ONLY = 2
 CF_FLAG_REUSE_PLAN = 4
+CF_FLAG_OPT_UNSTAGED = 8
 CF_PROBE_SMEM, CF_PROBE_L2, CF_PROBE_DSMEM, CF_PROBE_FP32 = 0, 1, 2, 3
 CF_DIST_SCALE01 = 1
 DIST_NAMES = ("euclidean", "manhattan", "minkowski", "jaccard", "cosine")
@@ -71,6 +72,8 @@ SIGNATURES = {
     "cf_similarity_backward": (_i32, [_p, _p, _p, _i32, C.POINTER(cf_params), _p, _p, _p, _p, _p, _p, _p,
                                       C.c_size_t, _p]),
     "cf_topk": (_i32, [_p, _i32, _i32, _i32, _p, _p, _p]),
+    "cf_topk_pairs": (_i32, [_p, _i32, _i32, _p, _p, _p]),
+    "cf_similarity_ws_size_any": (_i32, [_p, _p, _i32, C.POINTER(cf_params), _szp]),
     "cf_similarity_noalloc": (_i32, [_p, _p, _p, _i32, C.POINTER(cf_params), _p, _p, _p, _p, _p, _p]),
     "cf_status_check": (_i32, [_p, _p]),
     "cf_distances_ws_size": (_i32, [_i32, _szp]),

@@ -193,7 +193,7 @@ def tune_info(tune: int) -> dict:
 
 
 def match(pa: Pack, pb: Pack, pairs, X: torch.Tensor, *, ws: Workspace | None = None, stream=None,
-          optimal: bool = False) -> Result:
+          optimal: bool = False, flags: int = 0) -> Result:
     """Greedy (or, with ``optimal``, maximum-weight) matching and scores of
     caller-given matrices (cf_match with X)."""
     L = B.lib()
@@ -205,7 +205,7 @@ def match(pa: Pack, pb: Pack, pairs, X: torch.Tensor, *, ws: Workspace | None = 
     mt = torch.empty(int(m_off[-1]), dtype=torch.int32, device=dev)
     d_pairs = torch.from_numpy(pairs_np).to(dev)
     ws = ws or Workspace(dev)
-    prm = B.params(match_mode=B.CF_MATCH_OPTIMAL if optimal else B.CF_MATCH_GREEDY)
+    prm = B.params(match_mode=B.CF_MATCH_OPTIMAL if optimal else B.CF_MATCH_GREEDY, flags=flags)
     wbuf = ws.get(ws_size(pa, pb, pairs_np, prm))
     X = X.contiguous()
     st = _stream_ptr(stream)
@@ -279,12 +279,51 @@ def ward(points: torch.Tensor, stream=None):
     return merge, height, size
 
 
-def topk(scores: torch.Tensor, k: int, stream=None):
+def topk_pairs(idx: torch.Tensor, rows: torch.Tensor | None = None, *, out: torch.Tensor | None = None,
+               stream=None) -> torch.Tensor:
+    """The winners' pair list of a top-k on the device (cf_topk_pairs):
+    int32 [Q k, 2] with (rows[q] or q, idx[q, r]) for every query q and rank r."""
+    idx = idx.contiguous()
+    Q, k = idx.shape
+    if out is None:
+        out = torch.empty(Q * k, 2, dtype=torch.int32, device=idx.device)
+    B.check(B.lib().cf_topk_pairs(idx.data_ptr(), Q, k, _ptr(rows), out.data_ptr(), _stream_ptr(stream)))
+    return out
+
+
+def ws_size_any(pa: Pack, pb: Pack, P: int, prm: B.cf_params | None = None) -> int:
+    """Workspace bytes for any P pairs of these packs (cf_similarity_ws_size_any)."""
+    n = C.c_size_t(0)
+    B.check(B.lib().cf_similarity_ws_size_any(pa.host_ptr, pb.host_ptr, int(P), C.byref(prm) if prm else None,
+                                              C.byref(n)))
+    return n.value
+
+
+def similarity_dev(pa: Pack, pb: Pack, d_pairs: torch.Tensor, omega: torch.Tensor, alpha: float = 0.8, K: int = 40,
+                   *, scores: torch.Tensor | None = None, match: torch.Tensor | None = None, ws: Workspace,
+                   ws_bytes: int, tune: int = 0, stream=None) -> None:
+    """cf_similarity on a pair list that lives only on the device (int32
+    [P, 2], e.g. from topk_pairs): scores and / or matchings into the given
+    tensors (match needs sum of n_a over the pairs entries; its offsets are
+    the prefix sums of n_a in pair order).  Nothing is read back and no
+    status is checked, so the call can be captured in a CUDA graph."""
+    P = int(d_pairs.shape[0])
+    prm = B.params(alpha, K, tune=tune)
+    wbuf = ws.get(ws_bytes)
+    B.check(B.lib().cf_similarity(pa.dev.data_ptr(), pb.dev.data_ptr(), d_pairs.data_ptr(), P, C.byref(prm),
+                                  omega.contiguous().data_ptr(), None, _ptr(scores), _ptr(match), wbuf.data_ptr(),
+                                  ws_bytes, _stream_ptr(stream)))
+
+
+def topk(scores: torch.Tensor, k: int, stream=None, out: tuple | None = None):
     """Per-row top-k of a [Q, C] float32 score matrix: (values, column indices)."""
     s = scores.contiguous()
     Q, Cn = s.shape
-    top = torch.empty(Q, k, dtype=torch.float32, device=s.device)
-    idx = torch.empty(Q, k, dtype=torch.int32, device=s.device)
+    if out is not None:
+        top, idx = out
+    else:
+        top = torch.empty(Q, k, dtype=torch.float32, device=s.device)
+        idx = torch.empty(Q, k, dtype=torch.int32, device=s.device)
     B.check(B.lib().cf_topk(s.data_ptr(), Q, Cn, k, top.data_ptr(), idx.data_ptr(), _stream_ptr(stream)))
     return top, idx
 

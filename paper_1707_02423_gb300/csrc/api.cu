@@ -229,7 +229,7 @@ cf_status check_params(const cf_params* p) {
     return fail(CF_ERR_INVALID_ARG, "unknown norm_mode %d", p->norm_mode);
   if (p->match_mode != CF_MATCH_GREEDY && p->match_mode != CF_MATCH_OPTIMAL)
     return fail(CF_ERR_INVALID_ARG, "unknown match_mode %d", p->match_mode);
-  const uint32_t known = CF_FLAG_PER_PAIR_LAUNCH | CF_FLAG_PLAN_ONLY | CF_FLAG_REUSE_PLAN;
+  const uint32_t known = CF_FLAG_PER_PAIR_LAUNCH | CF_FLAG_PLAN_ONLY | CF_FLAG_REUSE_PLAN | CF_FLAG_OPT_UNSTAGED;
   if (p->flags & ~known) return fail(CF_ERR_INVALID_ARG, "unknown flags 0x%x", p->flags);
   if ((p->flags & CF_FLAG_PLAN_ONLY) && (p->flags & CF_FLAG_REUSE_PLAN))
     return fail(CF_ERR_INVALID_ARG, "CF_FLAG_PLAN_ONLY and CF_FLAG_REUSE_PLAN exclude each other");
@@ -344,6 +344,7 @@ CallArgs base_args(const void* d_pack_a, const void* d_pack_b, const int32_t* d_
     a.alpha = params->alpha;
     a.K = params->K;
     a.norm_mode = params->norm_mode;
+    a.opt_unstaged = (params->flags & CF_FLAG_OPT_UNSTAGED) ? 1 : 0;
   }
   a.omega = d_omega;
   a.ws = static_cast<unsigned char*>(d_ws);
@@ -531,6 +532,7 @@ cf_status cf_match(const void* d_pack_a, const void* d_pack_b, const int32_t* d_
     return fail(CF_ERR_INVALID_ARG, "unknown match_mode %d", params->match_mode);
   if (P == 0) return ok();
   CallArgs a = base_args(d_pack_a, d_pack_b, d_pairs, P, nullptr, nullptr, d_ws, ws_bytes);
+  a.opt_unstaged = params && (params->flags & CF_FLAG_OPT_UNSTAGED) ? 1 : 0;
   a.X_in = d_X_in;
   a.scores = d_scores;
   a.match = d_match;
@@ -635,6 +637,38 @@ cf_status cf_topk(const float* d_scores, int32_t Q, int32_t C, int32_t k, float*
   if (!d_scores || !d_top || !d_idx) return fail(CF_ERR_INVALID_ARG, "NULL buffer");
   cudaError_t e = launch_topk(d_scores, Q, C, k, d_top, d_idx, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "topk launch");
+  return ok();
+}
+
+cf_status cf_topk_pairs(const int32_t* d_idx, int32_t Q, int32_t k, const int32_t* d_rows, int32_t* d_pairs,
+                        cf_stream_t stream) {
+  if (Q < 0 || k < 1) return fail(CF_ERR_INVALID_ARG, "need Q >= 0 and k >= 1 (Q=%d k=%d)", Q, k);
+  if (Q == 0) return ok();
+  if (!d_idx || !d_pairs) return fail(CF_ERR_INVALID_ARG, "NULL buffer");
+  cudaError_t e = launch_topk_pairs(d_idx, Q, k, d_rows, d_pairs, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "topk pairs launch");
+  return ok();
+}
+
+cf_status cf_similarity_ws_size_any(const void* h_pack_a, const void* h_pack_b, int32_t P, const cf_params* params,
+                                    size_t* bytes) {
+  if (!bytes) return fail(CF_ERR_INVALID_ARG, "bytes is NULL");
+  if (P < 0) return fail(CF_ERR_INVALID_ARG, "P < 0");
+  if (params) {
+    cf_status s = check_params(params);
+    if (s) return s;
+  }
+  PackHeader ha, hb;
+  cf_status s = read_header(h_pack_a, &ha, "h_pack_a");
+  if (s) return s;
+  s = read_header(h_pack_b, &hb, "h_pack_b");
+  if (s) return s;
+  if (ha.F != hb.F) return fail(CF_ERR_INVALID_ARG, "packs have different F (%d vs %d)", ha.F, hb.F);
+  // every pair may be as large as the two largest CFGs, and every one may
+  // need a scratch slot (at most one per concurrently working CTA)
+  const int sms = device_sm_count();
+  const int64_t slots = std::min<int64_t>(P, 2 * (sms > 0 ? sms : 152));
+  *bytes = ws_layout(P).fixed_bytes + (size_t)slots * global_slot_bytes(ha.max_blocks, hb.max_blocks);
   return ok();
 }
 

@@ -35,6 +35,7 @@ struct CallArgs {
   int min_cls;  // smallest group level of the batched forward
   int ranked;   // matching policy of resident pairs (ClassCfg::ranked)
   int cluster;  // CTAs per cluster of the cluster tier, 0 = none
+  int opt_unstaged;  // optimal matching: skip the shared-memory slot pool (CF_FLAG_OPT_UNSTAGED)
 };
 
 // Batched forward kernel variants: 0 = 1024 threads per CTA, 1 = 512, 2 = 768.
@@ -96,6 +97,8 @@ cudaError_t launch_distances(const void* pack_a, const void* pack_b, const int32
 
 // Top-k per row.
 cudaError_t launch_topk(const float* scores, int Q, int C, int k, float* top, int32_t* idx, cudaStream_t s);
+// The winners' pair list from top-k indices.
+cudaError_t launch_topk_pairs(const int32_t* idx, int Q, int k, const int32_t* rows, int32_t* pairs, cudaStream_t s);
 
 
 }  // namespace cfsim

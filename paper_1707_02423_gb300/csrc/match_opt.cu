@@ -398,18 +398,18 @@ __device__ __forceinline__ void release_slots(unsigned long long* mask, int s, i
 
 // Takes k contiguous slots, waiting while other warps of the CTA hold them:
 // a warp sleeps only while the mask still holds the very value in which it
-// found no free run, so a release cannot go unseen.  -1 after kOptMaxWaits
-// polls (or if k can never fit).
-__device__ __forceinline__ int wait_slots(unsigned long long* mask, int k) {
+// found no free run, so a release cannot go unseen.  -1 after max_polls
+// polls (kOptMaxWaits; 0 under CF_FLAG_OPT_UNSTAGED) or if k can never fit.
+__device__ __forceinline__ int wait_slots(unsigned long long* mask, int k, int max_polls) {
   if (k <= 0 || k > kOptSlots) return -1;
-  for (int polls = 0; polls < kOptMaxWaits; ++polls) {
+  for (int polls = 0; polls < max_polls; ++polls) {
     const unsigned long long m = *reinterpret_cast<volatile unsigned long long*>(mask);
     const int s = first_run(m, k);
     if (s >= 0) {
       if (atomicCAS(mask, m, m | run_bits(s, k)) == m) return s;
       continue;  // the mask moved under us: look again at once
     }
-    while (polls < kOptMaxWaits && *reinterpret_cast<volatile unsigned long long*>(mask) == m) {
+    while (polls < max_polls && *reinterpret_cast<volatile unsigned long long*>(mask) == m) {
       __nanosleep(4000);  // long sleeps: waiting warps must not take issue slots from working ones
       ++polls;
     }
@@ -428,6 +428,7 @@ __global__ void __launch_bounds__(kOptNT) match_optimal_kernel(CallArgs a) {
   unsigned long long* ctr = reinterpret_cast<unsigned long long*>(&hdr->q_opt);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m_max = min(max(pack_max_blocks(a.pack_a), pack_max_blocks(a.pack_b)), opt_cap());
+  const int max_polls = a.opt_unstaged ? 0 : kOptMaxWaits;
   uint32_t n_pairs = 0;
   for (int c = 0; c < kNumClasses; ++c) n_pairs += hdr->n_class[c];
   if (m_max <= kOptRegCols) {
@@ -450,7 +451,7 @@ __global__ void __launch_bounds__(kOptNT) match_optimal_kernel(CallArgs a) {
       if (lane == 0) {
         // reserve room for the estimate, take a pair, keep what it needs
         const int k_est = *reinterpret_cast<volatile int*>(&s_kest);
-        int r0 = wait_slots(&s_mask, k_est);
+        int r0 = wait_slots(&s_mask, k_est, max_polls);
         q = take_pair(ctr, n_pairs);
         if (q >= 0) {
           const int p = (int)queue[q];
@@ -464,7 +465,7 @@ __global__ void __launch_bounds__(kOptNT) match_optimal_kernel(CallArgs a) {
             s0 = k > 0 ? r0 : -1;
           } else {
             if (r0 >= 0) release_slots(&s_mask, r0, k_est);
-            s0 = k > 0 ? wait_slots(&s_mask, k) : -1;
+            s0 = k > 0 ? wait_slots(&s_mask, k, max_polls) : -1;
           }
         } else if (r0 >= 0) {
           release_slots(&s_mask, r0, k_est);

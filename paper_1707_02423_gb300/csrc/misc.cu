@@ -70,7 +70,25 @@ __global__ void __launch_bounds__(kTopkNT) topk_kernel(const float* scores, int 
   }
 }
 
+// The pair list of the winners: pairs[2 (q k + r)] = rows ? rows[q] : q, and
+// pairs[2 (q k + r) + 1] = idx[q k + r], for every query q and rank r.
+__global__ void topk_pairs_kernel(const int32_t* idx, int Q, int k, const int32_t* rows, int32_t* pairs) {
+  const int64_t n = (int64_t)Q * k;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(t / k);
+    pairs[2 * t] = rows ? rows[q] : q;
+    pairs[2 * t + 1] = idx[t];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_topk_pairs(const int32_t* idx, int Q, int k, const int32_t* rows, int32_t* pairs, cudaStream_t s) {
+  const int64_t n = (int64_t)Q * k;
+  const int g = (int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
+  if (n > 0) topk_pairs_kernel<<<g, 256, 0, s>>>(idx, Q, k, rows, pairs);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_set_weights(CfAdj* out_adj, CfAdj* in_adj, const int32_t* in_eid, const int32_t* u2c,
                                int64_t n_user_edges, int64_t n_edges, const float* w_user, cudaStream_t s) {

@@ -162,6 +162,43 @@ def test_large_cfgs_global_class(tune):
     compare(w.cfgs_a, w.cfgs_a, w.pairs, w.F, tune=tune)
 
 
+def test_cfg3_sized_pair_global_tier(capsys):
+    """Two of the large-CFG workload's largest CFGs (1,959 x 1,968 blocks:
+    X holds 3.9 M entries, the global-memory tier) against the oracle, in
+    both orders: X and the score within max-abs 1e-5, the matching exact
+    where greedy decisions are clear.  X entries here are about 5e-4, so the
+    relative error of X is also bounded and reported beside the max-abs bar."""
+    w = config3()
+    n = np.array([c.n for c in w.cfgs_a])
+    a, b = (int(x) for x in np.argsort(n)[-2:])
+    cfgs = [w.cfgs_a[a], w.cfgs_a[b]]
+    pairs = np.array([[0, 1], [1, 0]], np.int32)
+    pa = api.Pack(cfgs, w.F, device=DEV)
+    res = api.similarity(pa, pa, pairs, torch.ones(w.F, device=DEV), 0.8, 40, want_x=True, want_match=True)
+    X = res.X.cpu().numpy()
+    sc = res.scores.cpu().numpy()
+    mt = res.match.cpu().numpy()
+    ref = oracle.similarity(cfgs[0], cfgs[1], np.ones(w.F), 0.8, 40)["X"]
+    worst_rel = 0.0
+    for p, R in ((0, ref), (1, ref.T)):
+        got = X[res.x_off[p]:res.x_off[p + 1]].reshape(R.shape)
+        err = np.abs(got - R)
+        assert err.max() <= ATOL_X, err.max()
+        rel = float((err / np.maximum(R, 1e-30)).max())
+        worst_rel = max(worst_rel, rel)
+        m_ref, s_ref = oracle.greedy_match(R)
+        m = mt[res.m_off[p]:res.m_off[p + 1]]
+        assert valid_matching(m, *R.shape)
+        if greedy_margin(R) > TIE_EPS:
+            assert np.array_equal(m, m_ref)
+            assert abs(float(sc[p]) - s_ref) <= ATOL_S
+        else:
+            assert eps_greedy(got, R, m, 2 * ATOL_X)
+    assert worst_rel <= 1e-3, worst_rel
+    with capsys.disabled():
+        print(f"\n  1959 x 1968 pair: max-abs error of X within {ATOL_X}, max relative error {worst_rel:.2e}")
+
+
 def test_full_cfg2_sampled():
     # the bench workload (all 19,900 pairs in one batched call), sampled outputs
     w = config2()

@@ -125,6 +125,44 @@ def test_many_pairs_through_the_slot_pool():
         assert abs(float(sc[p]) - value(X, m)) <= tol, p
 
 
+def test_unstaged_path_matches_the_oracle():
+    """The register form with every matrix read from global memory: the path
+    a warp takes when its bounded wait for shared-memory slots runs out
+    (forced for every pair by CF_FLAG_OPT_UNSTAGED), on near-rank-one
+    matrices of every width up to 128, against the oracle's optimum and the
+    staged path's assignment value."""
+    from gen import CFG
+
+    from paper_1707_02423_gb300 import _binding as B
+
+    rng = np.random.default_rng(11)
+    F = 2
+    sizes = np.concatenate([[1, 2, 31, 32, 33, 64, 65, 127, 128], rng.integers(1, 129, 21)])
+    cfgs = [CFG(int(n), np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.float32),
+                np.ones((int(n), F), np.float32)) for n in sizes]
+    pairs = np.array([(a, b) for a in range(len(cfgs)) for b in range(len(cfgs))], np.int32)
+    pairs = pairs[rng.permutation(len(pairs))[:400]]
+    mats = []
+    for a, b in pairs:
+        na, nb = int(sizes[a]), int(sizes[b])
+        X = np.outer(rng.uniform(0.5, 1, na), rng.uniform(0.5, 1, nb)) + 0.02 * rng.random((na, nb))
+        mats.append(X.astype(np.float32))
+    pa = api.Pack(cfgs, F, device=DEV)
+    Xd = torch.from_numpy(np.concatenate([m.ravel() for m in mats])).to(DEV)
+    un = api.match(pa, pa, pairs, Xd, optimal=True, flags=B.CF_FLAG_OPT_UNSTAGED)
+    st = api.match(pa, pa, pairs, Xd, optimal=True)
+    su, mu = un.scores.cpu().numpy(), un.match.cpu().numpy()
+    ss = st.scores.cpu().numpy()
+    for p in range(len(pairs)):
+        X = mats[p].astype(np.float64)
+        m = mu[un.m_off[p]:un.m_off[p + 1]]
+        assert valid_matching(m, *X.shape), p
+        _, s_ref = oracle.optimal_match(X)
+        tol = 1e-5 + 1e-6 * min(X.shape)
+        assert abs(value(X, m) - s_ref) <= tol, (p, X.shape, value(X, m), s_ref)
+        assert abs(float(su[p]) - float(ss[p])) <= tol, p
+
+
 def test_nan_row_sets_numeric_status():
     from gen import CFG
 

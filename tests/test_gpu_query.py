@@ -1,0 +1,116 @@
+"""The query step as one CUDA graph, end to end: scores of every query x
+corpus pair, top-k per query, the winners' pair list built on the device
+(cf_topk_pairs), and the winners' matchings and scores -- checked against the
+FP64 oracle on a reduced corpus (3 queries x 60 corpus CFGs of the query
+workload's distribution, n 5-400, F = 25, top-4)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from _helpers import ATOL_S, TIE_EPS, eps_greedy, greedy_margin, valid_matching  # noqa: E402
+from gen import config5  # noqa: E402
+from paper_1707_02423_gb300 import _binding as B  # noqa: E402
+from paper_1707_02423_gb300 import api  # noqa: E402
+
+DEV = "cuda:0"
+ALPHA, K = 0.8, 40
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1707_02423_gb300 import build
+
+    build.build()
+
+
+def test_query_graph_end_to_end():
+    nq, nc, k = 3, 60, 4
+    w = config5(nq, nc)
+    pa = api.Pack(w.cfgs_a, w.F, device=DEV)
+    pb = api.Pack(w.cfgs_b, w.F, device=DEV)
+    omega = torch.ones(w.F, device=DEV)
+    pairs = np.ascontiguousarray(w.pairs, np.int32)
+    P = len(pairs)
+    d_pairs = torch.from_numpy(pairs).to(DEV)
+    prm = B.params(ALPHA, K)
+    ws, mws = api.Workspace(DEV), api.Workspace(DEV)
+    ws_bytes = api.ws_size(pa, pb, pairs, prm)
+    mws_bytes = api.ws_size_any(pa, pb, nq * k, prm)
+    scores = torch.empty(P, device=DEV)
+    top = torch.empty(nq, k, device=DEV)
+    idx = torch.empty(nq, k, dtype=torch.int32, device=DEV)
+    win = torch.full((nq * k, 2), -1, dtype=torch.int32, device=DEV)
+    win_scores = torch.empty(nq * k, device=DEV)
+    n_q = np.array([c.n for c in w.cfgs_a])
+    win_match = torch.full((int(k * n_q.sum()),), -7, dtype=torch.int32, device=DEV)
+
+    def body():
+        api.similarity(pa, pb, pairs, omega, ALPHA, K, ws=ws, d_pairs=d_pairs, out={"scores": scores},
+                       check_status=False, ws_bytes=ws_bytes)
+        api.topk(scores.view(nq, nc), k, out=(top, idx))
+        api.topk_pairs(idx, out=win)
+        api.similarity_dev(pa, pb, win, omega, ALPHA, K, scores=win_scores, match=win_match, ws=mws,
+                           ws_bytes=mws_bytes)
+
+    body()
+    torch.cuda.synchronize()
+    g = api.Graph(DEV)
+    with g.capture():
+        body()
+    for t in (scores, top, win_scores):
+        t.fill_(-7.0)
+    win_match.fill_(-7)
+    g.launch()
+    torch.cuda.synchronize()
+    B.check(B.lib().cf_status_check(ws.get(ws_bytes).data_ptr(), None))
+    B.check(B.lib().cf_status_check(mws.get(mws_bytes).data_ptr(), None))
+    got = (scores.cpu().numpy().copy(), idx.cpu().numpy().copy(), win.cpu().numpy().copy(),
+           win_scores.cpu().numpy().copy(), win_match.cpu().numpy().copy())
+
+    # a second replay gives the same bits
+    g.launch()
+    torch.cuda.synchronize()
+    again = (scores.cpu().numpy(), idx.cpu().numpy(), win.cpu().numpy(), win_scores.cpu().numpy(),
+             win_match.cpu().numpy())
+    for x, y in zip(got, again):
+        assert np.array_equal(x, y)
+    sc, ix, wp, ws_, wm = got
+
+    # scores of every pair against the oracle
+    om = np.ones(w.F)
+    X_ref, s_ref = {}, np.zeros(P)
+    for p, (a, b) in enumerate(pairs):
+        X_ref[p] = oracle.similarity(w.cfgs_a[a], w.cfgs_b[b], om, ALPHA, K)["X"]
+        s_ref[p] = oracle.greedy_match(X_ref[p])[1]
+    assert np.abs(sc - s_ref).max() <= ATOL_S
+
+    # top-k: exactly the k largest GPU scores per query (ties: smaller column),
+    # and the oracle's top-k wherever its k-th and (k+1)-th scores are apart
+    S = sc.reshape(nq, nc)
+    R = s_ref.reshape(nq, nc)
+    for q in range(nq):
+        exact = np.lexsort((np.arange(nc), -S[q]))[:k]
+        assert np.array_equal(ix[q], exact)
+        ref_order = np.argsort(-R[q], kind="stable")
+        if R[q, ref_order[k - 1]] - R[q, ref_order[k]] > 2 * ATOL_S:
+            assert set(ix[q].tolist()) == set(ref_order[:k].tolist())
+
+    # the winners' pair list and their recomputed scores and matchings
+    assert np.array_equal(wp[:, 0], np.repeat(np.arange(nq), k))
+    assert np.array_equal(wp[:, 1], ix.ravel())
+    m_off = np.concatenate([[0], np.cumsum(n_q[wp[:, 0]])])
+    for t, (q, c) in enumerate(wp):
+        p = q * nc + c
+        assert abs(ws_[t] - sc[p]) <= 1e-6
+        m = wm[m_off[t]:m_off[t + 1]]
+        Xr = X_ref[p]
+        assert valid_matching(m, *Xr.shape)
+        if greedy_margin(Xr) > TIE_EPS:
+            assert np.array_equal(m, oracle.greedy_match(Xr)[0])
+        else:
+            assert eps_greedy(Xr, Xr, m, 2e-5)
