@@ -646,6 +646,21 @@ def run_ours(args):
     w = workload()
     P = len(w.pairs)
     pairs_np = np.ascontiguousarray(w.pairs, np.int32)
+    gather = None
+    if world > 1:
+        # the job: one copy of the workload's pair list per rank, partitioned
+        # across the ranks by LPT cost (each rank gets about P pairs, so the
+        # per-GPU work stays fixed as N grows), the pack replicated, and the
+        # scores all-gathered back into job order at the end of every step
+        from paper_1707_02423_gb300 import shard
+
+        job = np.tile(pairs_np, (world, 1))
+        ns = np.array([c.n for c in w.cfgs_a], np.int64)
+        es = np.array([len(set(zip(c.src.tolist(), c.dst.tolist()))) for c in w.cfgs_a], np.int64)
+        parts = shard.lpt_partition(shard.pair_costs(ns, ns, es, es, job), world)
+        pairs_np = np.ascontiguousarray(job[parts[rank]], np.int32)
+        gather = shard.ScoreGather(parts, len(job), dev)
+        P = len(pairs_np)
     pack = api.Pack(w.cfgs_a, w.F, device=dev)
     omega = torch.ones(w.F, dtype=torch.float32, device=dev)
     d_pairs = torch.from_numpy(pairs_np).to(dev)
@@ -697,6 +712,8 @@ def run_ours(args):
             g_plan.launch(stream)
             ev[i][1].record(stream)
             g_fwd.launch(stream)
+            if gather is not None:
+                gather(out["scores"])  # the exchange step: every rank gets the job's scores
             ev[i][2].record(stream)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
@@ -705,7 +722,7 @@ def run_ours(args):
     tot_ms = max_over_ranks(float(sum(step_ms)), world, dev)
     B.check(B.lib().cf_status_check(ws.get(ws_bytes).data_ptr(), int(stream.cuda_stream)))
     ms_per_step = tot_ms / args.steps
-    value = job_rate(P, world, ms_per_step)
+    value = job_rate(len(w.pairs), world, ms_per_step)  # world copies of the workload per step
 
     # ---- per-pair form: one launch per pair, same math
     pp_steps = 2
@@ -760,7 +777,10 @@ def run_ours(args):
 
     if rank != 0:
         return
-    onchip, flops, x_elems, m_elems = algorithmic(w, K_ITERS)
+    import dataclasses
+
+    # this rank's pairs (the whole workload at N = 1)
+    onchip, flops, x_elems, m_elems = algorithmic(dataclasses.replace(w, pairs=pairs_np), K_ITERS)
     fwd_mean_s = statistics.mean(fwd_ms) * 1e-3
     clk = clk.summary()
     props = torch.cuda.get_device_properties(dev)
@@ -782,7 +802,10 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "pairs": P, "n_cfgs": len(w.cfgs_a), "F": w.F, "K": K_ITERS,
+        "config": {"workload": WORKLOAD, "pairs": len(w.pairs) * world, "pairs_per_rank": P,
+                   "parallelism": (f"dp{world}: one copy of the pair list per rank, partitioned over the ranks by "
+                                   "LPT cost, pack replicated, scores all-gathered every step") if world > 1 else
+                                  "one GPU", "n_cfgs": len(w.cfgs_a), "F": w.F, "K": K_ITERS,
                    "alpha": ALPHA, "l2": "flushed between steps (256 MiB write, outside the step events)",
                    "step": "two CUDA-graph launches: plan (workspace reset + 3 kernels), forward (queue reset + "
                            "persistent kernel); sum of per-step CUDA events",
