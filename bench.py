@@ -75,14 +75,21 @@ def algorithmic(w, K):
     HBM bytes: the pack (read once), the pair list, scores and matchings.
     FLOPs: attribute term n_a n_b (2F + 3) plus per iteration 4 per gathered
     pair and 5 per entry."""
-    n = np.array([c.n for c in w.cfgs_a], np.int64)
-    e = np.array([len(set(zip(c.src.tolist(), c.dst.tolist()))) for c in w.cfgs_a], np.int64)
+    na, ea = _sizes(w.cfgs_a)
+    nb, eb = _sizes(w.cfgs_b)
     a, b = w.pairs[:, 0], w.pairs[:, 1]
-    nn = n[a] * n[b]
-    ee = e[a] * e[b]
+    nn = na[a] * nb[b]
+    ee = ea[a] * eb[b]
     onchip = int((K * 4 * (2 * ee + 2 * nn)).sum())
     flops = int((nn * (2 * w.F + 3) + K * (4 * ee + 5 * nn)).sum())
-    return onchip, flops, int(nn.sum()), int(n[a].sum())
+    return onchip, flops, int(nn.sum()), int(na[a].sum())
+
+
+def _sizes(cfgs):
+    """Blocks and distinct edges of every CFG (int64 arrays)."""
+    n = np.array([c.n for c in cfgs], np.int64)
+    e = np.array([len(set(zip(c.src.tolist(), c.dst.tolist()))) for c in cfgs], np.int64)
+    return n, e
 
 
 def algorithmic_bwd(w, K):
@@ -100,11 +107,11 @@ def algorithmic_bwd(w, K):
       + 4 (4 n_a n_b)              -- Ybar pass: Xbar, Y_{k+1} read; Zbar, Y_k written
       + 4 (4 e_a e_b)              -- edge terms: Zbar and Y_k at both ends of each pair of edges
     Returns (bytes, flops) with flops = 2 per gathered pair and edge term."""
-    n = np.array([c.n for c in w.cfgs_a], np.int64)
-    e = np.array([len(set(zip(c.src.tolist(), c.dst.tolist()))) for c in w.cfgs_a], np.int64)
+    na, ea = _sizes(w.cfgs_a)
+    nb, eb = _sizes(w.cfgs_b)
     a, b = w.pairs[:, 0], w.pairs[:, 1]
-    nn = n[a] * n[b]
-    ee = e[a] * e[b]
+    nn = na[a] * nb[b]
+    ee = ea[a] * eb[b]
     S = 1
     while S * S < K:
         S += 1
@@ -267,107 +274,103 @@ def host_cores() -> int:
     return max(1, min(32, n))
 
 
-_POOL_WORKLOAD = None
+def _oracle_task(task):
+    """One chunk of oracle work in a spawned worker: (kind, items) -> count.
 
-
-def _pool_init(name):
-    global _POOL_WORKLOAD
-    _POOL_WORKLOAD = workload(name)
-
-
-def _pool_pairs(idx):
+    kind "score": steps 1-5 of a pair (X_K, greedy matching, score);
+    "grad": the same and the reverse-mode gradient; "optimal": X_K and the
+    maximum-weight assignment; "dist": the five resized Table 1 distances;
+    "ward": a score matrix of seeded scores and its Ward linkage."""
     import oracle
+    from oracle import distances as odist
+    from oracle import ward as oward
 
-    w = _POOL_WORKLOAD
-    om = np.ones(w.F)
-    for p in idx:
-        a, b = w.pairs[p]
-        oracle.pair_score(w.cfgs_a[a], w.cfgs_b[b], om, ALPHA, K_ITERS)
-    return len(idx)
+    kind, items = task
+    for it in items:
+        if kind == "score":
+            a, b, F = it
+            oracle.pair_score(a, b, np.ones(F), ALPHA, K_ITERS)
+        elif kind == "grad":
+            a, b, F = it
+            oracle.score_gradient(a, b, np.ones(F), ALPHA, K_ITERS, gbar=1.0)
+        elif kind == "optimal":
+            a, b, F = it
+            oracle.optimal_match(oracle.similarity(a, b, np.ones(F), ALPHA, K_ITERS)["X"])
+        elif kind == "dist":
+            a, b, _ = it
+            odist.pair_distances(a, b, 3.0)
+        else:
+            n_cfg, pairs, seed = it
+            scores = np.random.default_rng(seed).uniform(1.0, 1.3, len(pairs))
+            oward.linkage(oward.score_matrix(n_cfg, pairs, scores))
+    return len(items)
 
 
 class OraclePool:
     """The FP64 oracle as it stands on `cores` worker processes, one thread
-    each, over independent pairs (the per-pair arithmetic is unchanged).  The
-    workers are spawned, not forked, so a pool started after CUDA
-    initialisation is safe."""
+    each, over independent units of work (the per-unit arithmetic is
+    unchanged).  Each task carries its own CFGs, so no worker regenerates a
+    workload.  The workers are spawned, not forked, so a pool started after
+    CUDA initialisation is safe."""
 
-    def __init__(self, name: str, cores: int):
+    def __init__(self, cores: int):
         import multiprocessing as mp
 
         self.cores = cores
-        self.pool = mp.get_context("spawn").Pool(cores, initializer=_pool_init, initargs=(name,))
+        self.pool = mp.get_context("spawn").Pool(cores)
 
-    def run(self, idx, chunk: int = 2) -> int:
-        idx = [int(i) for i in idx]
-        parts = [idx[i:i + chunk] for i in range(0, len(idx), chunk)]
-        return sum(self.pool.map(_pool_pairs, parts, chunksize=1))
-
-    def rate(self, idx) -> float:
-        """Pairs per second over idx (workers already started)."""
-        t0 = time.perf_counter()
-        n = self.run(idx)
-        return n / (time.perf_counter() - t0)
+    def run(self, kind, items, chunk: int = 1) -> int:
+        parts = [(kind, items[i:i + chunk]) for i in range(0, len(items), chunk)]
+        return sum(self.pool.map(_oracle_task, parts, chunksize=1))
 
     def close(self):
         self.pool.close()
         self.pool.join()
 
 
+# the oracle's unit of work per workload (bench.py --workload ...)
+ORACLE_KIND = {"cfg2": "score", "cfg3": "score", "cfg4": "grad", "cfg5": "score", "dist": "dist",
+               "optimal": "optimal", "ward": "ward"}
+
+
+def _oracle_items(name, w, idx):
+    if ORACLE_KIND[name] == "ward":
+        pairs = np.ascontiguousarray(w.pairs, np.int32)
+        return [(len(w.cfgs_a), pairs, int(s)) for s in idx]
+    return [(w.cfgs_a[int(w.pairs[p][0])], w.cfgs_b[int(w.pairs[p][1])], w.F) for p in idx]
+
+
 def cpu_oracle(w, seconds: float, seed: int = 0, name: str = "cfg2"):
     """The oracle on all host cores, on a seeded random sample of the
-    workload's pairs sized for about `seconds` of work (at most every pair):
-    (pairs/s, pairs timed, seconds, cores)."""
+    workload's units (pairs; for Ward, linkages of seeded scores) sized for
+    about `seconds` of work (at most every pair): (rate, units timed,
+    seconds, cores, what the sample is)."""
     cores = host_cores()
-    order = np.random.default_rng(seed).permutation(len(w.pairs))
-    pool = OraclePool(name, cores)
+    kind = ORACLE_KIND[name]
+    n_units = len(w.pairs) if kind != "ward" else 1 << 30
+    order = (np.random.default_rng(seed).permutation(len(w.pairs)) if kind != "ward"
+             else np.arange(4 * cores + 100000))
+    pool = OraclePool(cores)
     try:
-        pool.run(order[:2 * cores])  # starts every worker (spawn + imports), untimed
-        est = pool.rate(order[2 * cores:4 * cores])
-        n = int(min(len(order) - 4 * cores, max(4 * cores, est * seconds)))
-        sample = order[4 * cores:4 * cores + n]
+        pool.run(kind, _oracle_items(name, w, order[:cores]))  # starts every worker (spawn + imports), untimed
         t0 = time.perf_counter()
-        done = pool.run(sample)
+        pool.run(kind, _oracle_items(name, w, order[cores:3 * cores]))
+        est = 2 * cores / (time.perf_counter() - t0)
+        n = int(min(n_units - 3 * cores, max(2 * cores, est * seconds), len(order) - 3 * cores))
+        # a workload smaller than the warm-up and the estimate is timed whole
+        sample = order[3 * cores:3 * cores + n] if n >= cores else order[:min(len(order), n_units)]
+        t0 = time.perf_counter()
+        done = pool.run(kind, _oracle_items(name, w, sample))
         dt = time.perf_counter() - t0
     finally:
         pool.close()
-    return done / dt, done, dt, cores
-
-
-def cpu_next(name, w, seconds: float):
-    """The oracle as it stands, single-threaded, on a bounded sample of the
-    distances / optimal-matching / Ward workload: (rate in the workload's
-    unit, count, seconds, sample description).  Ward's sample is the score
-    matrix and linkage of seeded synthetic scores (the same shape)."""
-    import oracle
-    from oracle import distances as odist
-    from oracle import ward as oward
-
-    rng = np.random.default_rng(0)
-    t0 = time.perf_counter()
-    done = 0
-    if name == "ward":
-        scores = rng.uniform(1.0, 1.3, len(w.pairs))
-        while True:
-            oward.linkage(oward.score_matrix(len(w.cfgs_a), w.pairs, scores))
-            done += 1
-            if time.perf_counter() - t0 >= seconds:
-                break
-        dt = time.perf_counter() - t0
-        return done / dt, done, dt, f"{done} score matrices + Ward linkages of 200 CFGs (seeded scores)"
-    order = rng.permutation(len(w.pairs))
-    om = np.ones(w.F)
-    for p in order:
-        a, b = w.pairs[p]
-        if name == "dist":
-            odist.pair_distances(w.cfgs_a[a], w.cfgs_b[b], 3.0)
-        else:
-            oracle.optimal_match(oracle.similarity(w.cfgs_a[a], w.cfgs_b[b], om, ALPHA, K_ITERS)["X"])
-        done += 1
-        if time.perf_counter() - t0 >= seconds and done >= 20:
-            break
-    dt = time.perf_counter() - t0
-    return done / dt, done, dt, f"{done} seeded random pairs of the workload, single-threaded FP64 oracle"
+    what = {"score": "seeded random pairs of the workload (X_K, greedy matching, score)",
+            "grad": "seeded random pairs of the workload (forward and reverse-mode gradient)",
+            "optimal": "seeded random pairs of the workload (X_K and the maximum-weight assignment)",
+            "dist": "seeded random pairs of the workload (resized transition matrices, five distances)",
+            "ward": "score matrices of seeded scores of the workload's pairs and their Ward linkages"}[kind]
+    desc = (f"{done} {what} in {dt:.1f} s, FP64 oracle (numpy/scipy) on {cores} processes of one thread each")
+    return done / dt, done, dt, cores, desc
 
 
 def dist_setup(n_gpus):
@@ -414,18 +417,21 @@ def run_reference(args):
     w = workload()
     cores = host_cores()
     order = np.random.default_rng(1).permutation(len(w.pairs))
-    pool = OraclePool("cfg2", cores)
+    pool = OraclePool(cores)
     try:
-        pool.run(order[:2 * cores])  # starts every worker (spawn + imports), untimed
-        est = pool.rate(order[2 * cores:4 * cores])
+        pool.run("score", _oracle_items("cfg2", w, order[:cores]))  # starts every worker, untimed
+        t0 = time.perf_counter()
+        pool.run("score", _oracle_items("cfg2", w, order[cores:3 * cores]))
+        est = 2 * cores / (time.perf_counter() - t0)
         # size each step so that warmup + steps take about args.ref_seconds
         per_step = int(min(len(order), max(2 * cores, args.ref_seconds * est / (args.steps + args.warmup))))
         sample = order[:per_step]
+        items = _oracle_items("cfg2", w, sample)
         for _ in range(args.warmup):
-            pool.run(sample)
+            pool.run("score", items)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            pool.run(sample)
+            pool.run("score", items)
         dt = time.perf_counter() - t0
     finally:
         pool.close()
@@ -598,11 +604,54 @@ def make_query_step(w, pa, pb, omega, d_pairs, ws, tune):
     return replay, P, 2 * n_fwd + 2
 
 
-def run_workload(args):
-    """--workload cfg3 / cfg4 / cfg5 / dist / optimal / ward: one JSON line for
-    that workload alone (the last three with the oracle timed beside it)."""
+def onchip_peak(kind, f_mhz=None):
+    """A measured on-chip peak (cf_probe) in GB/s at the SM clock f_mhz (the
+    probe's own clock when None), with its description."""
     import torch
 
+    from paper_1707_02423_gb300 import _binding as B
+    from paper_1707_02423_gb300 import api
+
+    pr = api.probe(kind, reps=3)
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    f = f_mhz or pr["sm_mhz"]
+    name = {B.CF_PROBE_SMEM: "shared-memory loads", B.CF_PROBE_L2: "L2 re-reads (volatile, L1 bypassed)",
+            B.CF_PROBE_DSMEM: "distributed-shared-memory loads (2-CTA clusters)"}.get(kind, "FP32 FMA")
+    unit = "B" if kind != B.CF_PROBE_FP32 else "FLOP"
+    peak = pr["per_clk_sm"] * n_sm * f * 1e6 / 1e9
+    desc = (f"of measured: cf_probe {name} {pr['per_clk_sm']:.1f} {unit}/clk/SM ({pr['rate'] / 1e9:.0f} G{unit}/s "
+            f"at {pr['sm_mhz']:.0f} MHz) x {n_sm} SMs x {f:.0f} MHz")
+    return peak, desc, pr
+
+
+def prune_demo(w, scores):
+    """Query pruning (the next row of the query workload), measured: a
+    corpus CFG could be skipped for query q only if an upper bound on s(q, c)
+    fell below q's k-th best score.  The only admissible bound the measure
+    gives is s <= sqrt(min(n_q, n_c)) (a sum of min(n_q, n_c) entries of a
+    nonnegative X with |X|_F = 1, Cauchy-Schwarz; tight for a general X);
+    an attribute-only term cannot do better, because the attribute term's
+    share of X is at most 1 - alpha and the propagation term is unbounded by
+    it.  Returns the counts of this run."""
+    nq, nc, k = w.meta["n_query"], w.meta["n_corpus"], w.meta["top_k"]
+    S = np.asarray(scores, np.float64).reshape(nq, nc)
+    kth = -np.sort(-S, axis=1)[:, k - 1]
+    n_q = np.array([c.n for c in w.cfgs_a], np.float64)
+    n_c = np.array([c.n for c in w.cfgs_b], np.float64)
+    bound = np.sqrt(np.minimum(n_q[:, None], n_c[None, :]))
+    return {"bound": "s <= sqrt(min(n_q, n_c))", "pairs": int(S.size),
+            "prunable_pairs": int((bound < kth[:, None]).sum()),
+            "smallest_bound": float(bound.min()), "largest_kth_best_score": float(kth.max()),
+            "largest_score": float(S.max())}
+
+
+def run_workload(args):
+    """--workload cfg3 / cfg4 / cfg5 / dist / optimal / ward: one JSON line for
+    that workload alone, with the oracle timed on all host cores beside it,
+    and the roofline of the bandwidth-bound ones."""
+    import torch
+
+    from paper_1707_02423_gb300 import _binding as B
     from paper_1707_02423_gb300 import api
 
     world, rank, local = dist_setup(args.gpus)
@@ -617,6 +666,7 @@ def run_workload(args):
         return
     mps = tot / args.steps
     unit = UNITS.get(args.workload, UNIT)
+    clocks = clk.summary()
     line = {
         "metric": METRIC, "value": job_rate(P, world, mps), "unit": unit, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -624,12 +674,31 @@ def run_workload(args):
         "config": {"workload": WORKLOADS[args.workload], "pairs": P,
                    "l2": "flushed between steps (256 MiB write, outside the step events)",
                    "tune": api.tune_info(tune)},
-        "gpu_launches": launches * args.steps, "clocks": clk.summary(),
+        "gpu_launches": launches * args.steps, "clocks": clocks,
     }
-    if args.workload in ("dist", "optimal", "ward"):
-        v, n, dt, what = cpu_next(args.workload, workload(args.workload), args.cpu_seconds)
-        line["cpu_baseline"] = {"value": v, "unit": unit, "cores": 1, "kind": "oracle",
-                                "sample": f"{what} in {dt:.1f} s"}
+    w = workload(args.workload)
+    if args.workload in ("cfg3", "cfg4", "cfg5"):
+        # algorithmic on-chip bytes of the step (the forward's rule; the
+        # adjoint's for cfg4) over the step time, against the measured peak of
+        # the memory the iterations run from: L2 for the large CFGs (X in
+        # scratch slots), shared memory for the others
+        onchip = algorithmic(w, K_ITERS)[0]
+        if args.workload == "cfg4":
+            onchip += algorithmic_bwd(w, K_ITERS)[0]
+        kind = B.CF_PROBE_L2 if args.workload == "cfg3" else B.CF_PROBE_SMEM
+        peak, desc, _ = onchip_peak(kind, clocks["sm_mhz"])
+        achieved = onchip / (mps * 1e-3) / 1e9
+        line["roofline"] = {"bound": "l2" if kind == B.CF_PROBE_L2 else "smem",
+                            "kernel": {"cfg3": "fwd_batched_kernel / fwd_cluster_kernel (global-memory tier)",
+                                       "cfg4": "the whole forward + adjoint step",
+                                       "cfg5": "the whole query step (forward kernels, top-k, winners' matching)"}[
+                                           args.workload],
+                            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                            "traffic": None, "algorithmic_bytes_per_step": onchip, "peak_source": desc}
+    if args.workload == "cfg5":
+        line["pruning"] = prune_demo(w, step.scores.cpu().numpy())
+    v, n, dt, cores, desc = cpu_oracle(w, args.cpu_seconds, name=args.workload)
+    line["cpu_baseline"] = {"value": v, "unit": unit, "cores": cores, "kind": "oracle", "sample": desc}
     print(json.dumps(line), flush=True)
 
 
@@ -794,10 +863,15 @@ def run_ours(args):
     traffic = profiled_traffic(os.path.join(ROOT, "paper_1707_02423_gb300", "csrc", "forward.cu"))
     cpu_baseline = None  # the oracle is timed at N = 1 only
     if world == 1:
-        cpu_v, cpu_n, cpu_dt, cpu_cores = cpu_oracle(w, args.cpu_seconds)
-        cpu_baseline = {"value": cpu_v, "unit": UNIT, "cores": cpu_cores, "kind": "oracle",
-                        "sample": f"{cpu_n} seeded random pairs of the workload in {cpu_dt:.1f} s, FP64 oracle "
-                                  f"(numpy/scipy) on {cpu_cores} processes of one thread each"}
+        cpu_v, cpu_n, cpu_dt, cpu_cores, cpu_desc = cpu_oracle(w, args.cpu_seconds)
+        cpu_baseline = {"value": cpu_v, "unit": UNIT, "cores": cpu_cores, "kind": "oracle", "sample": cpu_desc}
+    probes = {}
+    for nm, kind in (("l2", B.CF_PROBE_L2), ("dsmem", B.CF_PROBE_DSMEM), ("fp32", B.CF_PROBE_FP32)):
+        pr = api.probe(kind, reps=3)
+        probes[nm] = {"per_clk_sm": pr["per_clk_sm"], "rate": pr["rate"], "sm_mhz": pr["sm_mhz"],
+                      "unit": "FLOP/s" if nm == "fp32" else "B/s"}
+    probes["smem"] = {"per_clk_sm": smem_probe["per_clk_sm"], "rate": smem_probe["rate"],
+                      "sm_mhz": smem_probe["sm_mhz"], "unit": "B/s"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -844,6 +918,7 @@ def run_ours(args):
         # cluster-tier kernel when the tune has one
         "gpu_launches": (4 + (1 if api.tune_info(tune)["cluster"] >= 2 else 0)) * args.steps,
         "clocks": clk,
+        "probes": probes,
         "wall_s_timed_region": t_wall,
     }
     print(json.dumps(line), flush=True)

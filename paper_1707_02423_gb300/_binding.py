@@ -8,7 +8,10 @@ from __future__ import annotations
 import ctypes as C
 import os
 
-LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcfsim.so")
+# The library this process loads: libcfsim.so beside this file, or another
+# build of it named by CFSIM_LIBRARY (e.g. the debug-bounds build,
+# libcfsim_debug.so, from build.build(variant="debug_bounds")).
+LIB_PATH = os.environ.get("CFSIM_LIBRARY") or os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcfsim.so")
 
 CF_OK = 0
 CF_NORM_FROB = 0

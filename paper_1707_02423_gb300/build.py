@@ -49,8 +49,27 @@ def _compile(src: str, extra: list[str], verbose: bool) -> str:
     return obj
 
 
-def build(verbose: bool = False, force: bool = False, extra: list[str] | None = None) -> str:
-    """Compile every CUDA source for sm_103a and link libcfsim.so; returns its path."""
+# Build variants: the product library, and a debug build whose kernels check
+# layouts, slots and staged indices (-DCF_DEBUG_BOUNDS; a failed check sets
+# the status word), loaded by setting CFSIM_LIBRARY to its path.
+VARIANTS = {None: (BUILD, LIB, []),
+            "debug_bounds": (os.path.join(HERE, "_build_debug"), os.path.join(HERE, "libcfsim_debug.so"),
+                             ["-DCF_DEBUG_BOUNDS"])}
+
+
+def build(verbose: bool = False, force: bool = False, extra: list[str] | None = None,
+          variant: str | None = None) -> str:
+    """Compile every CUDA source for sm_103a and link the library (libcfsim.so,
+    or the variant's); returns its path."""
+    global BUILD, LIB
+    bdir, lib, vflags = VARIANTS[variant]
+    if variant is not None:
+        saved = (BUILD, LIB)
+        BUILD, LIB = bdir, lib
+        try:
+            return build(verbose, force, list(extra or []) + vflags, None)
+        finally:
+            BUILD, LIB = saved
     extra = list(extra or [])
     os.makedirs(BUILD, exist_ok=True)
     hdr_t = _headers_mtime()
@@ -58,7 +77,8 @@ def build(verbose: bool = False, force: bool = False, extra: list[str] | None = 
     for s in SOURCES:
         obj = os.path.join(BUILD, s + ".o")
         src_t = os.path.getmtime(os.path.join(CSRC, s))
-        if force or extra or not os.path.exists(obj) or os.path.getmtime(obj) < max(src_t, hdr_t):
+        if force or (extra and BUILD == VARIANTS[None][0]) or not os.path.exists(obj) or \
+                os.path.getmtime(obj) < max(src_t, hdr_t):
             todo.append(s)
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         list(ex.map(lambda s: _compile(s, extra, verbose), todo))
@@ -78,4 +98,5 @@ def build(verbose: bool = False, force: bool = False, extra: list[str] | None = 
 if __name__ == "__main__":
     v = "-v" in sys.argv
     extra = ["-Xptxas", "-v"] if "--ptxas-v" in sys.argv else None
-    print(build(verbose=v, force="--force" in sys.argv, extra=extra))
+    variant = "debug_bounds" if "--debug-bounds" in sys.argv else None
+    print(build(verbose=v, force="--force" in sys.argv, extra=extra, variant=variant))

@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/cfsim.h"
 #include "kernels.h"
 #include "layout.h"
@@ -23,6 +25,17 @@ using namespace cfsim;
 namespace {
 
 thread_local std::string g_err;
+
+// An NVTX range ("cfsim/...") around a host-side stretch of a call: pack,
+// plan, iterate (the persistent forward with the fused greedy matching),
+// match and backward show up on a profiler's timeline with the kernels they
+// enqueue.  Without a profiler attached NVTX calls do nothing.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 cf_status fail(cf_status s, const char* fmt, ...) {
   char buf[512];
@@ -418,6 +431,7 @@ cf_status cf_pack_info_get(const void* h_pack, cf_pack_info* info) {
 
 cf_status cf_pack_cfgs(const cf_cfg_view* cfgs, int32_t n_cfgs, int32_t F, void* d_pack, size_t bytes,
                        cf_stream_t stream) {
+  NvtxRange nv("cfsim/pack");
   size_t need = 0;
   cf_status s = build_pack(cfgs, n_cfgs, F, nullptr, 0, &need);
   if (s) return s;
@@ -498,12 +512,14 @@ cf_status cf_similarity(const void* d_pack_a, const void* d_pack_b, const int32_
     e = cudaMemsetAsync(static_cast<char*>(d_ws) + offsetof(WsHeader, q_next), 0, sizeof(uint32_t) * kNumClasses, st);
     if (e != cudaSuccess) return cuda_fail(e, "queue reset");
   } else {
+    NvtxRange nv("cfsim/plan");
     e = cudaMemsetAsync(d_ws, 0, sizeof(WsHeader), st);
     if (e != cudaSuccess) return cuda_fail(e, "workspace reset");
     e = launch_plan(a, fwd_class_cfg(tn.variant, a.min_cls, a.ranked, a.cluster), st);
     if (e != cudaSuccess) return cuda_fail(e, "plan launch");
   }
   if (!(params->flags & CF_FLAG_PLAN_ONLY)) {
+    NvtxRange nv("cfsim/iterate");
     e = launch_forward(a, tn.variant, (params->flags & CF_FLAG_PER_PAIR_LAUNCH) != 0, st);
     if (e != cudaSuccess) return cuda_fail(e, "forward launch");
     if (optimal) {
@@ -514,6 +530,7 @@ cf_status cf_similarity(const void* d_pack_a, const void* d_pack_b, const int32_
       a.X_in = d_X;
       a.scores = d_scores;
       a.match = d_match;
+      NvtxRange nm("cfsim/match");
       e = launch_match_optimal(a, st);
       if (e != cudaSuccess) return cuda_fail(e, "optimal matching launch");
     }
@@ -526,6 +543,7 @@ cf_status cf_match(const void* d_pack_a, const void* d_pack_b, const int32_t* d_
                    float* d_scores, void* d_ws, size_t ws_bytes, cf_stream_t stream) {
   if (!d_X_in) return cf_similarity(d_pack_a, d_pack_b, d_pairs, P, params, d_omega, nullptr, d_scores, d_match,
                                     d_ws, ws_bytes, stream);
+  NvtxRange nv("cfsim/match");
   cf_status s = check_device_call(d_pack_a, d_pack_b, d_pairs, P, d_ws, ws_bytes);
   if (s) return s;
   if (params && params->match_mode != CF_MATCH_GREEDY && params->match_mode != CF_MATCH_OPTIMAL)
@@ -608,6 +626,7 @@ cf_status cf_similarity_backward(const void* d_pack_a, const void* d_pack_b, con
   if (d_pack_a == d_pack_b && d_grad_w_b && d_grad_w_b != d_grad_w_a)
     return fail(CF_ERR_INVALID_ARG, "with one pack on both sides, d_grad_w_b must be NULL or equal d_grad_w_a");
   if (P == 0) return ok();
+  NvtxRange nv("cfsim/backward");
   int variant = 0, cluster = 0;
   bwd_config(params, &variant, &cluster);
   const BwdShape sh = bwd_shape(variant, cluster, params->K);

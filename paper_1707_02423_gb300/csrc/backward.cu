@@ -625,7 +625,7 @@ __device__ __forceinline__ float sweep(const SweepGeo& q, const float* cur, uint
 // accumulates there instead of in the slot.
 template <bool kCl>
 __device__ __forceinline__ void run_pair_bwd_r(const BwdCtx& cx, const BGeo& g, const RTeam<kCl>& tm,
-                                            unsigned char* region, size_t zbytes, float* gslot,
+                                            unsigned char* region, size_t zbytes, float* gslot, size_t slot_bytes,
                                             const uint32_t* rbase) {
   const Shape& s = g.s;
   const int C = kCl ? tm.C : 1, crank = kCl ? tm.rank : 0;
@@ -665,6 +665,10 @@ __device__ __forceinline__ void run_pair_bwd_r(const BwdCtx& cx, const BGeo& g, 
   float* gC = gR + n_so;
   float* B3 = reinterpret_cast<float*>(region + align_up((size_t)(reinterpret_cast<unsigned char*>(gC + e_col) - region), 16));
   const bool ehb_s = (size_t)(reinterpret_cast<unsigned char*>(B3) - region) + 4 * (size_t)nn <= zbytes;
+  // (uniform over the team: every thread skips the pair together)
+  if (!bounds_ok(cx.hdr, (size_t)(reinterpret_cast<unsigned char*>(gC + e_col) - region) <= zbytes, kSiteBwdRegion) ||
+      !bounds_ok(cx.hdr, bwd_res_slot_bytes(s.n_row, ld, cx.K) <= slot_bytes, kSiteBwdSlot))
+    return;
   const uint32_t buf_bytes = 4u * (uint32_t)nn;
   // row u as the gathers address it: a byte offset within this CTA's buffers,
   // or (a row with a neighbour outside the slab, cluster only) the cluster
@@ -675,7 +679,9 @@ __device__ __forceinline__ void run_pair_bwd_r(const BwdCtx& cx, const BGeo& g, 
     return (int)(rbase[o] + 4u * (uint32_t)((u - o * slab) * ld));
   };
   for (int k = t; k < e_col; k += G) {
-    const CfAdj a = ldg_adj(g.c_oadj + co0 + k), b = ldg_adj(g.c_iadj + ci0 + k);
+    CfAdj a = ldg_adj(g.c_oadj + co0 + k), b = ldg_adj(g.c_iadj + ci0 + k);
+    if (!bounds_ok(cx.hdr, (unsigned)a.nbr < (unsigned)n_col && (unsigned)b.nbr < (unsigned)n_col, kSiteBwdColNbr))
+      a.nbr = b.nbr = 0;
     cedge[k] = make_int2(4 * a.nbr, __float_as_int(a.w));
     cedge[e_col + k] = make_int2(4 * b.nbr, __float_as_int(b.w));
     gC[k] = 0.f;
@@ -711,13 +717,15 @@ __device__ __forceinline__ void run_pair_bwd_r(const BwdCtx& cx, const BGeo& g, 
     rq[lr] = make_int4(raddr(b0.nbr, remote), __float_as_int(b0.w), raddr(b1.nbr, remote), __float_as_int(b1.w));
     rr[lr] = make_int4(o0 - so0, o1 - so0, n_so + q0 - si0, n_so + q1 - si0);
     for (int e = o0; e < o1; ++e) {
-      const CfAdj a = ldg_adj(g.r_oadj + eo0 + e);
+      CfAdj a = ldg_adj(g.r_oadj + eo0 + e);
+      if (!bounds_ok(cx.hdr, (unsigned)a.nbr < (unsigned)s.n_row, kSiteBwdRowNbr)) a.nbr = i0;
       redge[e - so0] = make_int2(raddr(a.nbr, remote), __float_as_int(a.w));
       rsrc[e - so0] = (lr * ld * 4) | rflag;
       gR[e - so0] = 0.f;
     }
     for (int e = q0; e < q1; ++e) {
-      const CfAdj b = ldg_adj(g.r_iadj + ei0 + e);
+      CfAdj b = ldg_adj(g.r_iadj + ei0 + e);
+      if (!bounds_ok(cx.hdr, (unsigned)b.nbr < (unsigned)s.n_row, kSiteBwdRowNbr)) b.nbr = i0;
       redge[n_so + e - si0] = make_int2(raddr(b.nbr, remote), __float_as_int(b.w));
     }
   }
@@ -1137,7 +1145,8 @@ __global__ void __launch_bounds__(NT, 1) bwd_big_kernel(CallArgs a, int n_cta) {
         run_pair_bwd(cx, bwd_pair(cx, p), reinterpret_cast<float*>(slot), tm, reinterpret_cast<float*>(smem));
       } else {
         const RTeam<true> rt{cta, &st, C, rank};
-        run_pair_bwd_r<true>(cx, make_bgeo(cx, p, cc), rt, smem, kBwdSmem, reinterpret_cast<float*>(slot), st.rbase);
+        run_pair_bwd_r<true>(cx, make_bgeo(cx, p, cc), rt, smem, kBwdSmem, reinterpret_cast<float*>(slot), need,
+                             st.rbase);
       }
     }
   }
@@ -1188,7 +1197,9 @@ __global__ void __launch_bounds__(NT, 1) bwd_res_kernel(CallArgs a, int n_cta, i
       region = smem + (size_t)(t >> 5) * cc.z_wrp;
       slot = 15 + (t >> 5);
     }
-    float* gslot = reinterpret_cast<float*>(area_base + bwd_slot_at((size_t)(region - smem), ratio));
+    const size_t ro = (size_t)(region - smem);
+    float* gslot = reinterpret_cast<float*>(area_base + bwd_slot_at(ro, ratio));
+    const size_t gslot_bytes = bwd_slot_at(ro + group_region(level, cc), ratio) - bwd_slot_at(ro, ratio);
     const uint32_t count = cx.hdr->n_class[level];
     for (;;) {
       if (grp.rank == 0) sh.p[slot] = atomicAdd(&cx.hdr->q_next[level], 1u);
@@ -1198,7 +1209,7 @@ __global__ void __launch_bounds__(NT, 1) bwd_res_kernel(CallArgs a, int n_cta, i
       if (q >= count) break;
       const RTeam<false> rt{grp, nullptr, 1, 0};
       run_pair_bwd_r<false>(cx, make_bgeo(cx, (int)cx.queue[qbase + q], cc), rt, region, group_region(level, cc),
-                            gslot, nullptr);
+                            gslot, gslot_bytes, nullptr);
     }
     qbase += count;
   }

@@ -60,6 +60,31 @@ __device__ __forceinline__ void set_status(WsHeader* h, int code, int info) {
   if (atomicCAS(&h->status, 0, code) == 0) h->status_info = info;
 }
 
+// Debug builds (compiled with -DCF_DEBUG_BOUNDS): checks of each pair's
+// shared-memory layout against its region, of scratch slots against the
+// workspace, and of staged neighbour indices against the CFG sizes.  A failed
+// check records CF_ERR_INVALID_ARG with the check's site code (>= 1000) in
+// the status word, and the caller skips the access.  In a normal build every
+// check is the constant true and compiles away.
+#ifdef CF_DEBUG_BOUNDS
+__device__ __forceinline__ bool bounds_ok(WsHeader* h, bool ok, int site) {
+  if (!ok && h) set_status(h, 1 /* CF_ERR_INVALID_ARG */, site);
+  return ok;
+}
+#else
+__device__ __forceinline__ bool bounds_ok(WsHeader*, bool, int) { return true; }
+#endif
+enum BoundsSite : int {
+  kSiteFwdRegion = 1001,  // a resident pair's layout exceeds its group's region
+  kSiteFwdRowNbr = 1002,  // a staged row neighbour outside the row graph
+  kSiteFwdColNbr = 1003,  // a staged column neighbour outside the column graph
+  kSiteFwdSlot = 1004,    // a global-class scratch slot past the workspace end
+  kSiteBwdRegion = 1011,  // an adjoint pair's layout exceeds its region
+  kSiteBwdSlot = 1012,    // an adjoint pair's slot exceeds its group's slot
+  kSiteBwdRowNbr = 1013,
+  kSiteBwdColNbr = 1014
+};
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -375,7 +375,8 @@ __device__ __forceinline__ void store_x(const Grp& grp, const Ctx& cx, const Geo
 // and columns (stride sF floats) when they fit.  After the iterations the
 // Ehat buffer holds the row matching state and the free iterate the column
 // state (int16).
-__device__ __forceinline__ void run_pair_s(const Ctx& cx, const Geo& g, const Group& grp, unsigned char* region) {
+__device__ __forceinline__ void run_pair_s(const Ctx& cx, const Geo& g, const Group& grp, unsigned char* region,
+                                           size_t zbytes) {
   const Shape& s = g.s;
   const int t = grp.rank;
   const int ld = s.ld;
@@ -397,8 +398,15 @@ __device__ __forceinline__ void run_pair_s(const Ctx& cx, const Geo& g, const Gr
   int* cptr = reinterpret_cast<int*>(cedge + 2 * e_col);
   int* nbusy = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(cptr) + align_up(8 * (size_t)(s.n_col + 1), 16));
   int16_t* brow = reinterpret_cast<int16_t*>(nbusy + 2);  // [n_busy][2]: row, row mod R
+  // (uniform over the group: every thread skips the pair together)
+  if (!bounds_ok(cx.hdr, (size_t)(reinterpret_cast<unsigned char*>(brow + 2 * s.n_row) - region) <= zbytes,
+                 kSiteFwdRegion))
+    return;
   for (int k = t; k < e_col; k += grp.size) {
-    const CfAdj a = ldg_adj(g.c_oadj + co0 + k), b = ldg_adj(g.c_iadj + ci0 + k);
+    CfAdj a = ldg_adj(g.c_oadj + co0 + k), b = ldg_adj(g.c_iadj + ci0 + k);
+    if (!bounds_ok(cx.hdr, (unsigned)a.nbr < (unsigned)s.n_col && (unsigned)b.nbr < (unsigned)s.n_col,
+                   kSiteFwdColNbr))
+      a.nbr = b.nbr = 0;
     cedge[k] = make_int2(4 * a.nbr, __float_as_int(a.w));
     cedge[e_col + k] = make_int2(4 * b.nbr, __float_as_int(b.w));
   }
@@ -418,7 +426,10 @@ __device__ __forceinline__ void run_pair_s(const Ctx& cx, const Geo& g, const Gr
     rr[i] = make_int4(o0, o1, e_row + q0, e_row + q1);
   }
   for (int k = t; k < e_row; k += grp.size) {
-    const CfAdj a = ldg_adj(g.r_oadj + eo0 + k), b = ldg_adj(g.r_iadj + ei0 + k);
+    CfAdj a = ldg_adj(g.r_oadj + eo0 + k), b = ldg_adj(g.r_iadj + ei0 + k);
+    if (!bounds_ok(cx.hdr, (unsigned)a.nbr < (unsigned)s.n_row && (unsigned)b.nbr < (unsigned)s.n_row,
+                   kSiteFwdRowNbr))
+      a.nbr = b.nbr = 0;
     redge[k] = make_int2(4 * ld * a.nbr, __float_as_int(a.w));
     redge[e_row + k] = make_int2(4 * ld * b.nbr, __float_as_int(b.w));
   }
@@ -810,7 +821,8 @@ __global__ void __launch_bounds__(NT, 1) fwd_batched_kernel(CallArgs a, int per_
     const uint64_t nslots = need ? cx.scratch_bytes / need : 0;
     if (nslots == 0) {
       if (blockIdx.x == 0 && t == 0) set_status(cx.hdr, 2 /* CF_ERR_WORKSPACE */, -1);
-    } else if (blockIdx.x < nslots) {
+    } else if (blockIdx.x < nslots &&
+               bounds_ok(cx.hdr, ((size_t)blockIdx.x + 1) * need <= cx.scratch_bytes, kSiteFwdSlot)) {
       float* slot = reinterpret_cast<float*>(cx.scratch + (size_t)blockIdx.x * need);
       for (;;) {
         if (t == 0) s_p[0] = atomicAdd(&cx.hdr->q_next[kClassGlobal], 1u);
@@ -879,7 +891,7 @@ __global__ void __launch_bounds__(NT, 1) fwd_batched_kernel(CallArgs a, int per_
         }
         break;
       }
-      run_pair_s(cx, g, grp, region);
+      run_pair_s(cx, g, grp, region, group_region(level, cc));
       if (single) break;
     }
     qbase += single ? 0u : n[level];

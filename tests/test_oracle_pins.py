@@ -403,3 +403,28 @@ def test_pins_catch_planted_mistakes(monkeypatch, golden_dir):
     monkeypatch.setattr(isorank, "greedy_match", bad_tie)
     assert not check_hand_one_iteration(golden_dir)
     monkeypatch.setattr(isorank, "greedy_match", real_g)
+
+
+def test_query_pruning_bound_holds_and_is_tight():
+    """The bound a query search could prune with: s <= sqrt(min(n_a, n_b)),
+    the Cauchy-Schwarz bound on a sum of min(n_a, n_b) entries of a
+    nonnegative X with |X|_F = 1.  It holds on every pair of the parity and
+    query workloads' distributions, for every alpha; and no smaller bound in
+    sizes alone exists, since X = I / sqrt(n) (two identical chains with
+    one-hot attributes at alpha = 0) reaches it exactly."""
+    from gen import config1, config5
+
+    for w in (config1(), config5(2, 12)):
+        for alpha in (0.0, 0.5, 0.8, 0.95):
+            for a, b in w.pairs:
+                A, B = w.cfgs_a[a], w.cfgs_b[b]
+                X = oracle.similarity(A, B, np.ones(w.F), alpha, 40)["X"]
+                assert abs(np.linalg.norm(X) - 1.0) < 1e-12 and X.min() >= 0.0
+                s = oracle.greedy_match(X)[1]
+                assert s <= np.sqrt(min(A.n, B.n)) + 1e-12
+    # tightness: n blocks, no edges, attributes one-hot per block
+    n = 5
+    cfg = CFG(n, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.float32),
+              np.eye(n, dtype=np.float32))
+    X = oracle.similarity(cfg, cfg, np.ones(n), 0.0, 40)["X"]
+    assert abs(oracle.greedy_match(X)[1] - np.sqrt(n)) < 1e-12
