@@ -635,9 +635,70 @@ __device__ __forceinline__ void run_pair_bwd_r(const BwdCtx& cx, const BGeo& g, 
   const int slab = kCl ? ceil_div(s.n_row, C) : s.n_row;
   const int i0 = crank * slab;
   const int rows = max(0, min(s.n_row, i0 + slab) - i0);
-  const int nn = slab * ld;
   const float gp = __ldg(cx.gbar + g.p);
   if (gp == 0.f) return;  // every term is linear in g: nothing to add (uniform over the team)
+  const int ib = min(i0, s.n_row);  // a CTA past the last row has an empty slab
+  const int eo0 = __ldg(g.r_optr), ei0 = __ldg(g.r_iptr);
+  const int so0 = __ldg(g.r_optr + ib) - eo0, so1 = __ldg(g.r_optr + ib + rows) - eo0;
+  const int si0 = __ldg(g.r_iptr + ib) - ei0, si1 = __ldg(g.r_iptr + ib + rows) - ei0;
+  const int n_so = so1 - so0, n_si = si1 - si0;
+  const int co0 = __ldg(g.c_optr), ci0 = __ldg(g.c_iptr);
+  const int e_col = __ldg(g.c_optr + n_col) - co0;
+
+  // ---- cluster: the halo.  The rows of other CTAs that this slab's rows
+  // read are kept as extra rows of this CTA's own buffers (after its slab)
+  // and copied from their owners once per sweep, so every gather and edge
+  // term reads this CTA's shared memory.  Every CTA lays its buffers out for
+  // the cluster's largest halo; a pair whose halo does not fit in some CTA's
+  // region reads those rows through distributed shared memory instead.
+  int H = 0, hmax = 0;
+  bool halo = false;
+  ClState* hs = tm.st;
+  if (kCl) {
+    const int nw = ceil_div(s.n_row, 32);
+    const bool bitmap_ok = s.n_row <= kHaloMaxRows;
+    for (int k = t; k < 64; k += G) hs->hbits[k] = 0u;
+    __syncthreads();
+    if (bitmap_ok)
+      for (int lr = t; lr < rows; lr += G) {
+        const int i = i0 + lr;
+        for (int e = __ldg(g.r_optr + i) - eo0, e1 = __ldg(g.r_optr + i + 1) - eo0; e < e1; ++e) {
+          const int u = __ldg(&g.r_oadj[eo0 + e].nbr);
+          if ((u < i0 || u >= i0 + slab) && (unsigned)u < (unsigned)s.n_row) atomicOr(&hs->hbits[u >> 5], 1u << (u & 31));
+        }
+        for (int e = __ldg(g.r_iptr + i) - ei0, e1 = __ldg(g.r_iptr + i + 1) - ei0; e < e1; ++e) {
+          const int u = __ldg(&g.r_iadj[ei0 + e].nbr);
+          if ((u < i0 || u >= i0 + slab) && (unsigned)u < (unsigned)s.n_row) atomicOr(&hs->hbits[u >> 5], 1u << (u & 31));
+        }
+      }
+    __syncthreads();
+    if (t == 0) {
+      int run = 0;
+      for (int k = 0; k < nw && bitmap_ok; ++k) {
+        hs->hpre[k] = run;
+        run += __popc(hs->hbits[k]);
+      }
+      hs->hcnt = bitmap_ok && run <= kHaloRows ? run : (1 << 28);
+    }
+    __syncthreads();
+    H = hs->hcnt;
+    if (H <= kHaloRows)
+      for (int u = t; u < s.n_row; u += G)
+        if (hs->hbits[u >> 5] & (1u << (u & 31)))
+          hs->hrow[hs->hpre[u >> 5] + __popc(hs->hbits[u >> 5] & ((1u << (u & 31)) - 1u))] = (int16_t)u;
+    cl_sync();  // every CTA's count is published
+    for (int o = 0; o < C; ++o) hmax = max(hmax, (int)cl_ld_u32(cl_map(&hs->hcnt, o)));
+    // the layout this CTA would need with hmax halo rows per buffer
+    const size_t nn_h = (size_t)(slab + hmax) * ld;
+    const size_t end_h = align_up(12 * nn_h, 16) + 48 * (size_t)slab + 8 * (size_t)(n_so + n_si) + 16 * (size_t)e_col +
+                         align_up(8 * (size_t)(n_col + 1), 16) + align_up(8 + 4 * (size_t)slab, 16) +
+                         8 * (size_t)(n_so + e_col);
+    if (t == 0) hs->hfit = hmax <= kHaloRows && end_h <= zbytes ? 1 : 0;
+    cl_sync();
+    halo = true;
+    for (int o = 0; o < C; ++o) halo = halo && cl_ld_u32(cl_map(&hs->hfit, o)) != 0u;
+  }
+  const int nn = (slab + (halo ? hmax : 0)) * ld;
   float* B0 = reinterpret_cast<float*>(region);
   float* B1 = B0 + nn;
   float* B2 = B1 + nn;
@@ -648,13 +709,6 @@ __device__ __forceinline__ void run_pair_bwd_r(const BwdCtx& cx, const BGeo& g, 
 
   // ---- stage the lists (as the forward does), plus each edge's source and
   // a gradient accumulator per edge
-  const int ib = min(i0, s.n_row);  // a CTA past the last row has an empty slab
-  const int eo0 = __ldg(g.r_optr), ei0 = __ldg(g.r_iptr);
-  const int so0 = __ldg(g.r_optr + ib) - eo0, so1 = __ldg(g.r_optr + ib + rows) - eo0;
-  const int si0 = __ldg(g.r_iptr + ib) - ei0, si1 = __ldg(g.r_iptr + ib + rows) - ei0;
-  const int n_so = so1 - so0, n_si = si1 - si0;
-  const int co0 = __ldg(g.c_optr), ci0 = __ldg(g.c_iptr);
-  const int e_col = __ldg(g.c_optr + n_col) - co0;
   int2* cedge = redge + (n_so + n_si);
   int* cptr = reinterpret_cast<int*>(cedge + 2 * e_col);
   int* nbusy = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(cptr) + align_up(8 * (size_t)(n_col + 1), 16));
@@ -670,13 +724,39 @@ __device__ __forceinline__ void run_pair_bwd_r(const BwdCtx& cx, const BGeo& g, 
       !bounds_ok(cx.hdr, bwd_res_slot_bytes(s.n_row, ld, cx.K) <= slot_bytes, kSiteBwdSlot))
     return;
   const uint32_t buf_bytes = 4u * (uint32_t)nn;
-  // row u as the gathers address it: a byte offset within this CTA's buffers,
-  // or (a row with a neighbour outside the slab, cluster only) the cluster
+  // row u as the gathers address it: a byte offset within this CTA's buffers
+  // (a row of the slab, or a halo row after it), or -- a row with a
+  // neighbour outside the slab, in a cluster without the halo -- the cluster
   // address of row u in its owner's buffer 0
   auto raddr = [&](int u, bool remote) -> int {
+    if (kCl && halo && (u < i0 || u >= i0 + slab)) {
+      const int h = hs->hpre[u >> 5] + __popc(hs->hbits[u >> 5] & ((1u << (u & 31)) - 1u));
+      return (slab + h) * ld * 4;
+    }
     if (!remote) return (u - i0) * ld * 4;
     const int o = u / slab;
     return (int)(rbase[o] + 4u * (uint32_t)((u - o * slab) * ld));
+  };
+  // copy this CTA's halo rows of a buffer (byte offset boff from buffer 0)
+  // from their owners, then a CTA barrier; the owners' rows are final (a
+  // cluster barrier came after they were written)
+  auto pull = [&](float* buf, uint32_t boff) {
+    for (int h = wp; h < H; h += NW) {
+      const int u = hs->hrow[h];
+      const int o = u / slab;
+      const uint32_t src = rbase[o] + boff + 4u * (uint32_t)((u - o * slab) * ld);
+      float* dst = buf + (size_t)(slab + h) * ld;
+      for (int c0 = 0; c0 < n_col; c0 += 256) {
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (c0 + 32 * q + lane < n_col) v[q] = cl_ld_f32(src + 4u * (uint32_t)(c0 + 32 * q + lane));
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (c0 + 32 * q + lane < n_col) dst[c0 + 32 * q + lane] = v[q];
+      }
+    }
+    __syncthreads();
   };
   for (int k = t; k < e_col; k += G) {
     CfAdj a = ldg_adj(g.c_oadj + co0 + k), b = ldg_adj(g.c_iadj + ci0 + k);
@@ -697,7 +777,7 @@ __device__ __forceinline__ void run_pair_bwd_r(const BwdCtx& cx, const BGeo& g, 
     const int o0 = __ldg(g.r_optr + i) - eo0, o1 = __ldg(g.r_optr + i + 1) - eo0;
     const int q0 = __ldg(g.r_iptr + i) - ei0, q1 = __ldg(g.r_iptr + i + 1) - ei0;
     bool remote = false;
-    if (kCl) {
+    if (kCl && !halo) {
       for (int e = o0; e < o1; ++e) {
         const int u = __ldg(&g.r_oadj[eo0 + e].nbr);
         remote |= u < i0 || u >= i0 + slab;
@@ -819,6 +899,7 @@ __device__ __forceinline__ void run_pair_bwd_r(const BwdCtx& cx, const BGeo& g, 
     float* nxt = (k & 1) ? B0 : B1;
     float* dst = yloc(k + 1) + gbase;
     const float ca = 0.5f * alpha * sk;
+    if (kCl && halo) pull(const_cast<float*>(cur), (k & 1) ? buf_bytes : 0u);
     ss = sweep<kCl, false>(sq, cur, (k & 1) ? buf_bytes : 0u, ca, B2, nxt, dst, nullptr);
     const float yy = tm.sum(ss, par);
     par ^= 1;
@@ -867,6 +948,7 @@ __device__ __forceinline__ void run_pair_bwd_r(const BwdCtx& cx, const BGeo& g, 
         float* nxt = (u & 1) ? B0 : B1;
         float* dst = yloc(k + 1) + gbase;
         const float ca = 0.5f * alpha * ginv[k];
+        if (kCl && halo) pull(const_cast<float*>(cur), (u & 1) ? buf_bytes : 0u);
         sweep<kCl, false>(sq, cur, (u & 1) ? buf_bytes : 0u, ca, B2, nxt, dst, nullptr);
         tm.sync();
       }
@@ -892,6 +974,10 @@ __device__ __forceinline__ void run_pair_bwd_r(const BwdCtx& cx, const BGeo& g, 
       });
       tm.sync();
       // Xbar_k = 1/2 M(Zbar) and <Xbar_k, Y_k>
+      if (kCl && halo) {
+        pull(ZB, zoff);
+        pull(XK, xoff);
+      }
       acc = sweep<kCl, true>(sq, ZB, zoff, 0.5f, nullptr, XB, nullptr, XK);
       // edge terms T = Zbar[p,j] Y_k[q,v] + Y_k[p,j] Zbar[q,v] for row edge p->q, column edge j->v:
       // lanes take the column edges 32 at a time, warps the row edges; a row

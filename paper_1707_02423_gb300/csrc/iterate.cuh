@@ -208,7 +208,16 @@ struct ClState {
   uint32_t paddr[kMaxCluster];  // cluster address of each CTA's part[]
   uint32_t piaddr[kMaxCluster]; // cluster address of each CTA's parti[]
   uint32_t qaddr;               // cluster address of CTA 0's q
+  // the halo of a pair's slab (rows of other CTAs that its gathers read):
+  // a bitmap over the row graph, its per-word prefix counts, the rows in
+  // order, and this CTA's count / fit flag as the other CTAs read them
+  uint32_t hbits[64];
+  int hpre[64];
+  int16_t hrow[512];
+  int hcnt, hfit;
 };
+constexpr int kHaloRows = 512;   // halo rows a CTA may hold (hrow)
+constexpr int kHaloMaxRows = 2048;  // row-graph size the halo bitmap covers
 
 // Sum of v over every thread of the cluster, the same bits on every thread:
 // warps -> CTA (one CTA barrier) -> cluster (one cluster barrier; lane r
