@@ -158,6 +158,19 @@ def fwd_bwd_measure(dev, tune_cache, steps=5, warmup=3, bwd_tune=0):
             "bwd_flops": flops, "tune": api.tune_info(tune)}
 
 
+# A kernel configuration given on the command line (--tune) instead of the
+# autotuner's pick, so that a profile can be taken of a named configuration.
+FIXED_TUNE = 0
+
+
+def pick_tune(pa, pb, pairs_np, omega, tune_cache):
+    from paper_1707_02423_gb300 import api
+
+    if FIXED_TUNE:
+        return FIXED_TUNE
+    return api.autotune(pa, pb, pairs_np, omega, ALPHA, K_ITERS, cache_path=tune_cache)[0]
+
+
 def make_fwd_bwd(w, dev, tune_cache=None, bwd_tune=0):
     """(forward, adjoint, P, tune) callables of the gradient workload through
     the Python API, every buffer allocated up front."""
@@ -177,7 +190,7 @@ def make_fwd_bwd(w, dev, tune_cache=None, bwd_tune=0):
     x_off, m_off = api.out_offsets(pa, pb, pairs_np)
     out = {"scores": torch.empty(P, dtype=torch.float32, device=dev),
            "match": torch.empty(int(m_off[-1]), dtype=torch.int32, device=dev)}
-    tune, _ = api.autotune(pa, pb, pairs_np, omega, ALPHA, K_ITERS, cache_path=tune_cache)
+    tune = pick_tune(pa, pb, pairs_np, omega, tune_cache)
     ws_bytes = api.ws_size(pa, pb, pairs_np, prm)
     g = torch.ones(P, dtype=torch.float32, device=dev)
     grads = {"grad_w_a": torch.zeros(int(pa.info.n_user_edges), dtype=torch.float32, device=dev),
@@ -489,7 +502,7 @@ def make_step(name, dev, tune_cache=None, bwd_tune=0):
     x_off, m_off = api.out_offsets(pa, pb, pairs_np)
     out = {"scores": torch.empty(P, dtype=torch.float32, device=dev),
            "match": torch.empty(int(m_off[-1]), dtype=torch.int32, device=dev)}
-    tune, _ = api.autotune(pa, pb, pairs_np, omega, ALPHA, K_ITERS, cache_path=tune_cache)
+    tune = pick_tune(pa, pb, pairs_np, omega, tune_cache)
     # kernels per forward call: the three plan kernels, the persistent forward
     # and, under a cluster tune, the cluster-tier kernel; per adjoint call: the
     # three plan kernels, the accumulator reset, the adjoint and the scatter
@@ -745,7 +758,11 @@ def run_ours(args):
     # on-chip peak the iteration kernel is bound by, measured on this GPU
     smem_probe = api.probe(B.CF_PROBE_SMEM, reps=3)
     # kernel configuration: the autotuner's pick for this workload (cached per device and workload)
-    tune, tune_ms = api.autotune(pack, pack, pairs_np, omega, ALPHA, K_ITERS, cache_path=args.tune_cache)
+    tune_ms = None
+    if FIXED_TUNE:
+        tune = FIXED_TUNE
+    else:
+        tune, tune_ms = api.autotune(pack, pack, pairs_np, omega, ALPHA, K_ITERS, cache_path=args.tune_cache)
 
     def sim(flags):
         api.similarity(pack, pack, pairs_np, omega, ALPHA, K_ITERS, want_match=True, ws=ws, d_pairs=d_pairs,
@@ -808,6 +825,19 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     pp_ms = e0.elapsed_time(e1) / pp_steps
+    # the same launches spread over 32 streams: what remains of the gap is
+    # per-launch cost and one pair per SM, not the serialisation
+    api.similarity(pack, pack, pairs_np, omega, ALPHA, K_ITERS, want_match=True, ws=ws, d_pairs=d_pairs, out=out,
+                   check_status=False, per_pair=True, flags=B.CF_FLAG_PER_PAIR_STREAMS, tune=tune)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(pp_steps):
+        flush.zero_()
+        api.similarity(pack, pack, pairs_np, omega, ALPHA, K_ITERS, want_match=True, ws=ws, d_pairs=d_pairs,
+                       out=out, check_status=False, per_pair=True, flags=B.CF_FLAG_PER_PAIR_STREAMS, tune=tune)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pps_ms = e0.elapsed_time(e1) / pp_steps
 
     # ---- forward + adjoint on the gradient workload (256 pairs, n 10-300)
     fb = fwd_bwd_measure(dev, args.tune_cache)
@@ -908,7 +938,9 @@ def run_ours(args):
                                  "flops_per_launch": fb["bwd_flops"], "kernel_ms": fb["bwd_ms"],
                                  "peak_source": "of measured: the same shared-memory peak as the forward's line"}},
         "per_pair": {"value": P / (pp_ms * 1e-3), "unit": UNIT, "ms_per_step": pp_ms, "launches_per_step": P,
-                     "speedup_batched_over_per_pair": pp_ms / ms_per_step},
+                     "speedup_batched_over_per_pair": pp_ms / ms_per_step,
+                     "over_32_streams": {"value": P / (pps_ms * 1e-3), "ms_per_step": pps_ms,
+                                         "speedup_batched_over_it": pps_ms / ms_per_step}},
         "cpu_baseline": cpu_baseline,
         "e2e": {"value": world * P / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_s * 1e3,
@@ -934,9 +966,13 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=90.0,
                     help="--impl reference: oracle work per run (warmup + steps), in seconds")
     ap.add_argument("--workload", default="cfg2", choices=sorted(WORKLOADS))
+    ap.add_argument("--tune", type=int, default=0,
+                    help="kernel configuration id for the forward (0: the autotuner's pick)")
     ap.add_argument("--tune-cache", default=os.environ.get("CF_AUTOTUNE_CACHE") or
                     os.path.join(tempfile.gettempdir(), "cfsim_autotune.cache"))
     args = ap.parse_args()
+    global FIXED_TUNE
+    FIXED_TUNE = args.tune
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -85,10 +85,16 @@ enum {
                                         order, offsets) into the workspace                  */
   CF_FLAG_REUSE_PLAN = 1u << 2,      /* skip the plan: reuse the one a previous call with the
                                         same packs, pairs and workspace left there          */
-  CF_FLAG_OPT_UNSTAGED = 1u << 3     /* testing: under CF_MATCH_OPTIMAL every matrix is read
+  CF_FLAG_OPT_UNSTAGED = 1u << 3,    /* testing: under CF_MATCH_OPTIMAL every matrix is read
                                         from global memory instead of being staged in the
                                         kernel's shared-memory slot pool -- the path a warp
                                         takes when its bounded wait for slots runs out       */
+  CF_FLAG_PER_PAIR_STREAMS = 1u << 4 /* with CF_FLAG_PER_PAIR_LAUNCH: the launches are spread
+                                        over 32 streams forked from the caller's stream and
+                                        joined back to it (pair p on stream p mod 32, each
+                                        stream with its own scratch slot), so launches of the
+                                        plain form no longer run one after another; for
+                                        measuring what the batched form's gain is made of    */
 };
 
 typedef struct cf_params {

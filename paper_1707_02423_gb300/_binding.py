@@ -22,6 +22,7 @@ CF_FLAG_PER_PAIR_LAUNCH = 1
 CF_FLAG_PLAN_ONLY = 2
 CF_FLAG_REUSE_PLAN = 4
 CF_FLAG_OPT_UNSTAGED = 8
+CF_FLAG_PER_PAIR_STREAMS = 16
 CF_PROBE_SMEM, CF_PROBE_L2, CF_PROBE_DSMEM, CF_PROBE_FP32 = 0, 1, 2, 3
 CF_DIST_SCALE01 = 1
 DIST_NAMES = ("euclidean", "manhattan", "minkowski", "jaccard", "cosine")

@@ -242,7 +242,8 @@ cf_status check_params(const cf_params* p) {
     return fail(CF_ERR_INVALID_ARG, "unknown norm_mode %d", p->norm_mode);
   if (p->match_mode != CF_MATCH_GREEDY && p->match_mode != CF_MATCH_OPTIMAL)
     return fail(CF_ERR_INVALID_ARG, "unknown match_mode %d", p->match_mode);
-  const uint32_t known = CF_FLAG_PER_PAIR_LAUNCH | CF_FLAG_PLAN_ONLY | CF_FLAG_REUSE_PLAN | CF_FLAG_OPT_UNSTAGED;
+  const uint32_t known = CF_FLAG_PER_PAIR_LAUNCH | CF_FLAG_PLAN_ONLY | CF_FLAG_REUSE_PLAN | CF_FLAG_OPT_UNSTAGED |
+                         CF_FLAG_PER_PAIR_STREAMS;
   if (p->flags & ~known) return fail(CF_ERR_INVALID_ARG, "unknown flags 0x%x", p->flags);
   if ((p->flags & CF_FLAG_PLAN_ONLY) && (p->flags & CF_FLAG_REUSE_PLAN))
     return fail(CF_ERR_INVALID_ARG, "CF_FLAG_PLAN_ONLY and CF_FLAG_REUSE_PLAN exclude each other");
@@ -358,6 +359,7 @@ CallArgs base_args(const void* d_pack_a, const void* d_pack_b, const int32_t* d_
     a.K = params->K;
     a.norm_mode = params->norm_mode;
     a.opt_unstaged = (params->flags & CF_FLAG_OPT_UNSTAGED) ? 1 : 0;
+    a.pp_streams = (params->flags & CF_FLAG_PER_PAIR_STREAMS) ? kPerPairStreams : 0;
   }
   a.omega = d_omega;
   a.ws = static_cast<unsigned char*>(d_ws);
@@ -480,8 +482,10 @@ cf_status cf_similarity_ws_size(const void* h_pack_a, const void* h_pack_b, cons
   cf_status s = scan_pairs(h_pack_a, h_pack_b, h_pairs, P, nullptr, nullptr, &need, &ng);
   if (s) return s;
   // scratch slots for global-class pairs: one per concurrently working CTA
+  // (the plain form spread over streams: one per stream)
   int sms = device_sm_count();
   int64_t slots = std::min<int64_t>(ng, 2 * (sms > 0 ? sms : 152));
+  if (params && (params->flags & CF_FLAG_PER_PAIR_STREAMS) && ng > 0) slots = std::max<int64_t>(slots, kPerPairStreams);
   *bytes = ws_layout(P).fixed_bytes + (size_t)slots * need;
   return ok();
 }

@@ -30,6 +30,8 @@
 // pair.  The row graph's lists are staged once per pair in shared memory as
 // per-row edge ranges and {u * ld, w} entries, so a gather is two dependent
 // shared loads and the lanes sharing a row read the same words.
+#include <mutex>
+
 #include "device_common.cuh"
 #include "device_state.h"
 #include "iterate.cuh"
@@ -794,7 +796,7 @@ __host__ __device__ constexpr ClassCfg fwd_cfg(int min_cls = kClassWarp, int ran
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT, 1) fwd_batched_kernel(CallArgs a, int per_pair) {
+__global__ void __launch_bounds__(NT, 1) fwd_batched_kernel(CallArgs a, int per_pair, int pp_slot) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(16) float s_om[2 * kMaxF];  // omega, then sqrt(omega)
   __shared__ Ctx s_cx;
@@ -880,14 +882,16 @@ __global__ void __launch_bounds__(NT, 1) fwd_batched_kernel(CallArgs a, int per_
       if (q >= count) break;
       if (single && grp.rank == 0) s_p[slot] = 1u;  // the next pull ends the loop
       const Geo g = make_geo(cx, single ? per_pair : (int)cx.queue[qbase + q], cc);
-      if (g.s.cls == kClassGlobal) {  // only in the plain form: scratch slot 0
-        if (global_slot_bytes(g.na, g.nb) > cx.scratch_bytes) {
+      if (g.s.cls == kClassGlobal) {  // only in the plain form: the scratch slot of its stream
+        const size_t need = pp_slot > 0 ? (size_t)cx.hdr->slot_need : 0;
+        float* pslot = reinterpret_cast<float*>(cx.scratch + (size_t)pp_slot * need);
+        if (global_slot_bytes(g.na, g.nb) + (size_t)pp_slot * need > cx.scratch_bytes) {
           if (t == 0) set_status(cx.hdr, 2 /* CF_ERR_WORKSPACE */, per_pair);
         } else {
           if (staged_fits(g, cc.z_cta))
-            run_pair_g<true>(cx, g, cta, cta, reinterpret_cast<float*>(cx.scratch), smem);
+            run_pair_g<true>(cx, g, cta, cta, pslot, smem);
           else
-            run_pair_g<false>(cx, g, cta, cta, reinterpret_cast<float*>(cx.scratch), smem);
+            run_pair_g<false>(cx, g, cta, cta, pslot, smem);
         }
         break;
       }
@@ -1168,6 +1172,33 @@ __global__ void __launch_bounds__(kMatchNT) match_only_kernel(CallArgs a) {
   }
 }
 
+// Per device: the side streams and events of the plain form spread over
+// streams (CF_FLAG_PER_PAIR_STREAMS), created on first use.
+struct PerPairStreams {
+  cudaStream_t side[kPerPairStreams] = {};
+  cudaEvent_t fork = nullptr, join[kPerPairStreams] = {};
+  std::mutex mu;  // one fork / join sequence at a time (the events are shared)
+};
+
+cudaError_t per_pair_streams(PerPairStreams** out) {
+  static DeviceOnce once;
+  static PerPairStreams devs[kMaxDevices];
+  int dev = 0;
+  const cudaError_t e = once.run(
+      [](int d) {
+        PerPairStreams& ps = devs[d];
+        cudaError_t r = cudaEventCreateWithFlags(&ps.fork, cudaEventDisableTiming);
+        for (int k = 0; k < kPerPairStreams && r == cudaSuccess; ++k) {
+          r = cudaStreamCreateWithFlags(&ps.side[k], cudaStreamNonBlocking);
+          if (r == cudaSuccess) r = cudaEventCreateWithFlags(&ps.join[k], cudaEventDisableTiming);
+        }
+        return r;
+      },
+      &dev);
+  *out = e == cudaSuccess ? &devs[dev] : nullptr;
+  return e;
+}
+
 // Per device: the kernel's shared-memory limit and the SM count (the grid).
 template <int NT>
 cudaError_t fwd_init(int* n_sm) {
@@ -1191,10 +1222,27 @@ cudaError_t launch_fwd(const CallArgs& a, bool per_pair, cudaStream_t s) {
   int n_sm = 0;
   cudaError_t e = fwd_init<NT>(&n_sm);
   if (e != cudaSuccess) return e;
-  if (per_pair) {
-    for (int p = 0; p < a.P; ++p) fwd_batched_kernel<NT><<<1, NT, kFwdSmem, s>>>(a, p);
+  if (per_pair && a.pp_streams > 1) {
+    // the plain form spread over side streams forked from s and joined back:
+    // pair p on stream p mod S, with that stream's scratch slot
+    PerPairStreams* ps = nullptr;
+    e = per_pair_streams(&ps);
+    if (e != cudaSuccess) return e;
+    const int S = a.pp_streams < kPerPairStreams ? a.pp_streams : kPerPairStreams;
+    std::lock_guard<std::mutex> lk(ps->mu);
+    e = cudaEventRecord(ps->fork, s);
+    for (int k = 0; k < S && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(ps->side[k], ps->fork, 0);
+    for (int p = 0; p < a.P && e == cudaSuccess; ++p)
+      fwd_batched_kernel<NT><<<1, NT, kFwdSmem, ps->side[p % S]>>>(a, p, p % S);
+    for (int k = 0; k < S && e == cudaSuccess; ++k) {
+      e = cudaEventRecord(ps->join[k], ps->side[k]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ps->join[k], 0);
+    }
+    if (e != cudaSuccess) return e;
+  } else if (per_pair) {
+    for (int p = 0; p < a.P; ++p) fwd_batched_kernel<NT><<<1, NT, kFwdSmem, s>>>(a, p, 0);
   } else {
-    fwd_batched_kernel<NT><<<n_sm, NT, kFwdSmem, s>>>(a, -1);
+    fwd_batched_kernel<NT><<<n_sm, NT, kFwdSmem, s>>>(a, -1, 0);
   }
   return cudaGetLastError();
 }

@@ -36,7 +36,11 @@ struct CallArgs {
   int ranked;   // matching policy of resident pairs (ClassCfg::ranked)
   int cluster;  // CTAs per cluster of the cluster tier, 0 = none
   int opt_unstaged;  // optimal matching: skip the shared-memory slot pool (CF_FLAG_OPT_UNSTAGED)
+  int pp_streams;    // the plain per-pair form: streams its launches are spread over (0/1: the caller's)
 };
+
+// Streams the plain per-pair form may be spread over (CF_FLAG_PER_PAIR_STREAMS).
+constexpr int kPerPairStreams = 32;
 
 // Batched forward kernel variants: 0 = 1024 threads per CTA, 1 = 512, 2 = 768.
 int num_fwd_variants();

@@ -32,12 +32,13 @@ def _built():
 
 
 def compare(cfgs_a, cfgs_b, pairs, F, omega=None, alpha=0.8, K=40, per_pair=False, norm_mode=0,
-            check_x=True, sample=None, tune=0):
+            check_x=True, sample=None, tune=0, flags=0):
     pa = api.Pack(cfgs_a, F, device=DEV)
     pb = pa if cfgs_b is cfgs_a else api.Pack(cfgs_b, F, device=DEV)
     om = np.ones(F) if omega is None else np.asarray(omega, np.float64)
     res = api.similarity(pa, pb, pairs, torch.tensor(om, dtype=torch.float32, device=DEV), alpha, K,
-                         want_x=check_x, want_match=True, per_pair=per_pair, norm_mode=norm_mode, tune=tune)
+                         want_x=check_x, want_match=True, per_pair=per_pair, norm_mode=norm_mode, tune=tune,
+                         flags=flags)
     scores = res.scores.cpu().numpy()
     match = res.match.cpu().numpy()
     X = res.X.cpu().numpy() if check_x else None
@@ -90,6 +91,15 @@ def test_cfg2_subset_all_classes():
 def test_per_pair_form_matches_oracle():
     w = config2(14)
     compare(w.cfgs_a, w.cfgs_a, w.pairs, w.F, per_pair=True)
+
+
+def test_per_pair_form_over_streams_matches_oracle():
+    """The plain form with its launches spread over 32 streams: small pairs
+    and global-class pairs (each stream with its own scratch slot)."""
+    w = config2(14)
+    compare(w.cfgs_a, w.cfgs_a, w.pairs, w.F, per_pair=True, flags=B.CF_FLAG_PER_PAIR_STREAMS)
+    big = config3(3, 500, 900)
+    compare(big.cfgs_a, big.cfgs_a, big.pairs, big.F, per_pair=True, flags=B.CF_FLAG_PER_PAIR_STREAMS)
 
 
 @pytest.mark.parametrize("alpha,K", [(0.0, 40), (0.5, 7), (0.95, 40), (0.8, 0), (0.8, 1)])
