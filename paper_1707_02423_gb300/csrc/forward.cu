@@ -349,6 +349,167 @@ __device__ __forceinline__ float greedy_ranked(const Group& grp, const float* X,
   return grp.sum(sc, 0);
 }
 
+// a5-a6 as the sequential greedy itself, on one warp.
+//
+// Every entry gets an order key okey(x): unsigned comparison of keys is the
+// float order, NaN lowest (after -inf, where the greedy order visits it) and
+// -0 equal to +0; keys are >= 1 so that 0 marks a finished list.  Lists run
+// along the shorter side: a list is a row when n_col <= n_row, else a column,
+// and it ranks its len = min(n_row, n_col) elements by (key desc, index asc),
+// which is the greedy order (value desc, A index asc, B index asc) restricted
+// to the list in either orientation.  The whole group counts the ranks, len
+// comparisons per entry (the rounds of greedy_ranked rank both sides).  Then
+// one warp takes the greedy's entries in turn: the head of every live list is
+// its best live element, and the best head under the greedy order (key desc,
+// then (A, B) index asc) is the largest live entry, the one sequential greedy
+// takes next.  Its list and element die, and the lists whose head was that
+// element advance past dead elements.  Exactly len steps, each a warp-wide
+// max and min (redux.sync) over the heads held in registers (R per lane), with
+// no group barrier.
+// Shared memory: key n_row x ld (the free iterate); the ranked elements rk
+// (int16, nl x len) and then the dead flags (len bytes) over X_K, which the
+// keys replace; the ranked keys rkey (uint32, nl x len) over the Ehat buffer.
+// Returns the score on the group's rank 0; writes match[n_A] (-1 for
+// unmatched rows of A) if given.  A taken NaN entry sets CF_ERR_NUMERIC.
+__device__ __forceinline__ uint32_t okey(float x) {
+  if (x != x) return 1u;
+  if (x == 0.f) x = 0.f;
+  const uint32_t b = __float_as_uint(x);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float okey_value(uint32_t k) {
+  return k == 1u ? __int_as_float(0x7fffffff) : __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+template <int R>
+__device__ __noinline__ float greedy_seq_steps(int lane, bool swap, int nl, int len, const int16_t* rk,
+                                               const uint32_t* rkey, unsigned char* dead, int32_t* mo,
+                                               WsHeader* hdr, int pidx) {
+  // (A, B) index of element e of list l: (l, e), or (e, l) when swapped
+  auto tie = [&](int l, int e) -> uint32_t {
+    return swap ? ((uint32_t)e << 16) | (uint32_t)l : ((uint32_t)l << 16) | (uint32_t)e;
+  };
+  int cur[R], el[R];
+  uint32_t hk[R], ht[R];
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    const int l = lane + 32 * s;
+    cur[s] = 0;
+    el[s] = -1;
+    hk[s] = 0u;
+    ht[s] = 0xffffffffu;
+    if (l < nl) {
+      const int e = rk[l * len];
+      el[s] = e;
+      hk[s] = rkey[l * len];
+      ht[s] = tie(l, e);
+    }
+  }
+  float sc = 0.f;
+  for (int step = 0; step < len; ++step) {
+    uint32_t bk = 0u, bt = 0xffffffffu;
+#pragma unroll
+    for (int s = 0; s < R; ++s)
+      if (hk[s] > bk || (hk[s] == bk && ht[s] < bt)) {
+        bk = hk[s];
+        bt = ht[s];
+      }
+    const uint32_t mk = __reduce_max_sync(0xffffffffu, bk);
+    const uint32_t mt = __reduce_min_sync(0xffffffffu, bk == mk ? bt : 0xffffffffu);
+    if (mk == 0u) break;  // no live list (not reached: a live list remains while steps remain)
+    const int hi = (int)(mt >> 16), lo = (int)(mt & 0xffffu);
+    const int l = swap ? lo : hi, e = swap ? hi : lo;
+    if (lane == 0) {
+      dead[e] = 1;
+      sc += okey_value(mk);
+      if (mo) mo[hi] = lo;
+      if (mk == 1u && hdr) set_status(hdr, 6 /* CF_ERR_NUMERIC */, pidx);
+    }
+#pragma unroll
+    for (int s = 0; s < R; ++s)
+      if (lane + 32 * s == l) {  // the taken list
+        el[s] = -1;
+        hk[s] = 0u;
+        ht[s] = 0xffffffffu;
+      }
+    if (step + 1 == len) break;  // every element is taken
+    __syncwarp();                 // dead[e] is visible to the warp
+#pragma unroll
+    for (int s = 0; s < R; ++s)
+      if (el[s] == e) {  // its head died: the next live element of its list
+        const int base = (lane + 32 * s) * len;
+        int k = cur[s] + 1, v = -1;
+        uint32_t kv = 0u;
+        for (; k < len; ++k) {
+          v = rk[base + k];
+          kv = rkey[base + k];
+          if (!dead[v]) break;
+        }
+        cur[s] = k;
+        if (k < len) {
+          el[s] = v;
+          hk[s] = kv;
+          ht[s] = tie(lane + 32 * s, v);
+        } else {  // not reached: a live element remains while steps remain
+          el[s] = -1;
+          hk[s] = 0u;
+          ht[s] = 0xffffffffu;
+        }
+      }
+  }
+  return sc;
+}
+
+__device__ __forceinline__ float greedy_seq(const Group& grp, float* X, int ld, int n_row, int n_col, int tr,
+                                            uint32_t* key, uint32_t* rkey, int32_t* mo, WsHeader* hdr, int pidx) {
+  const int t = grp.rank, G = grp.size;
+  const bool rows = n_col <= n_row;
+  const int nl = rows ? n_row : n_col, len = rows ? n_col : n_row;
+  const int E = n_row * n_col;
+  for (int idx = t; idx < E; idx += G) {
+    const int r = idx / n_col, c = idx - r * n_col;
+    key[r * ld + c] = okey(X[r * ld + c]);
+  }
+  if (mo) {
+    const int nA = tr ? n_col : n_row;
+    for (int a = t; a < nA; a += G) mo[a] = -1;
+  }
+  grp.sync();
+  // rank of element e in list l: elements with a larger key, or an equal key
+  // and a smaller index (k >= 1, so k - 1 does not wrap)
+  int16_t* rk = reinterpret_cast<int16_t*>(X);
+  unsigned char* dead = reinterpret_cast<unsigned char*>(rk + nl * len);
+  for (int idx = t; idx < E; idx += G) {
+    const int r = idx / n_col, c = idx - r * n_col;
+    const uint32_t k = key[r * ld + c];
+    const int l = rows ? r : c, e = rows ? c : r;
+    const uint32_t* kp = rows ? key + r * ld : key + c;
+    const int st = rows ? 1 : ld;
+    int cnt = 0;
+#pragma unroll 4
+    for (int e2 = 0; e2 < len; ++e2) cnt += kp[e2 * st] > k - (uint32_t)(e2 < e);
+    rk[l * len + cnt] = (int16_t)e;
+    rkey[l * len + cnt] = k;
+  }
+  for (int e = t; e < len; e += G) dead[e] = 0;
+  grp.sync();
+  float sc = 0.f;
+  if (t < 32) {
+    const bool swap = rows == (tr != 0);
+    const int Rn = (nl + 31) >> 5;
+    if (Rn <= 1)
+      sc = greedy_seq_steps<1>(t, swap, nl, len, rk, rkey, dead, mo, hdr, pidx);
+    else if (Rn <= 2)
+      sc = greedy_seq_steps<2>(t, swap, nl, len, rk, rkey, dead, mo, hdr, pidx);
+    else if (Rn <= 4)
+      sc = greedy_seq_steps<4>(t, swap, nl, len, rk, rkey, dead, mo, hdr, pidx);
+    else
+      sc = greedy_seq_steps<8>(t, swap, nl, len, rk, rkey, dead, mo, hdr, pidx);
+  }
+  return sc;
+}
+constexpr int kSeqMaxLists = 256;
+
 // Write X_K (resident, possibly transposed, stride ld) to the caller's
 // row-major n_a x n_b output, coalesced on the global side.
 template <class Grp>
@@ -571,7 +732,12 @@ __device__ __forceinline__ void run_pair_s(const Ctx& cx, const Geo& g, const Gr
   if (cx.scores || cx.match) {
     int32_t* mo = cx.match ? cx.match + cx.m_off[g.p] : nullptr;
     const bool ranked = cx.ranked == 0 || (cx.ranked == 1 && 4 * grp.size <= (int)blockDim.x);
-    if (ranked && 5 * (size_t)(s.n_row + s.n_col) + 16 <= 4 * (size_t)nn) {  // room for the ranked lists' state
+    if (ranked && max(s.n_row, s.n_col) <= kSeqMaxLists) {
+      // keys in the free iterate, ranked elements over X_K, their keys over Ehat
+      const float sc = greedy_seq(grp, Xs, ld, s.n_row, s.n_col, s.tr, reinterpret_cast<uint32_t*>(freeb),
+                                  reinterpret_cast<uint32_t*>(ehb), mo, cx.hdr, g.p);
+      if (cx.scores && t == 0) cx.scores[g.p] = sc;
+    } else if (ranked && 5 * (size_t)(s.n_row + s.n_col) + 16 <= 4 * (size_t)nn) {  // room for the ranked lists' state
       const float sc = greedy_ranked(grp, Xs, ld, s.n_row, s.n_col, s.tr, reinterpret_cast<int16_t*>(ehb),
                                      reinterpret_cast<int16_t*>(ehb) + s.n_row * s.n_col,
                                      reinterpret_cast<unsigned char*>(freeb), mo, cx.hdr, g.p);
