@@ -31,6 +31,7 @@
 // per-row edge ranges and {u * ld, w} entries, so a gather is two dependent
 // shared loads and the lanes sharing a row read the same words.
 #include <mutex>
+#include <type_traits>
 
 #include "device_common.cuh"
 #include "device_state.h"
@@ -510,6 +511,114 @@ __device__ __forceinline__ float greedy_seq(const Group& grp, float* X, int ld, 
 }
 constexpr int kSeqMaxLists = 256;
 
+// a5-a6 for a global-class pair on one CTA: the rounds of greedy(), with
+// the row and column states in shared memory and both kinds of rescan
+// reading contiguous memory.  A row rescan (a warp per row) reads the row of
+// X_K; a column rescan (a warp per column) reads the row of X_K^T, written
+// once into free scratch by 32 x 32 tiles through shared memory.  (With X_K
+// in L2 or beyond, greedy()'s column scans -- one sector per lane per load --
+// were the matching's cost.)  Each lane keeps four loads in flight.  The
+// results are greedy()'s: the same rounds, the same per-line best under
+// (value desc, index asc), NaN never taken.
+// sm: rb (n_row), cb, tg (n_col each) as int16, then a 32 x 33 float tile
+// per warp; XT: n_col x n_row floats of free scratch.
+__device__ __forceinline__ void scan_line(const float* x, const int16_t* st, int n, int lane, float& bv, int& bi) {
+  bv = -CUDART_INF_F;
+  bi = 0x7fffffff;
+  for (int c0 = lane; c0 < n; c0 += 128) {
+    float v[4];
+    bool ok[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = c0 + 32 * u;
+      ok[u] = c < n && st[c] > (int16_t)-3;
+      v[u] = c < n ? x[c] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (ok[u] && v[u] > bv) {  // a lane's columns ascend: strict > keeps the smallest
+        bv = v[u];
+        bi = c0 + 32 * u;
+      }
+  }
+  warp_argmax(bv, bi);
+}
+
+__device__ __noinline__ float greedy_g(const Group& grp, const float* X, int n_row, int n_col, float* XT,
+                                       unsigned char* sm, int32_t* mo, WsHeader* hdr, int pidx) {
+  const int t = grp.rank, G = grp.size, lane = t & 31, w = grp.warp(), NW = grp.nwarps();
+  int16_t* rb = reinterpret_cast<int16_t*>(sm);
+  int16_t* cb = rb + n_row;
+  int16_t* tg = cb + n_col;
+  float* tile = reinterpret_cast<float*>(align_up(reinterpret_cast<size_t>(tg + n_col), 16)) + w * 32 * 33;
+  for (int r = t; r < n_row; r += G) rb[r] = (int16_t)-2;
+  for (int c = t; c < n_col; c += G) {
+    cb[c] = (int16_t)-2;
+    tg[c] = 0;
+  }
+  // X^T by 32 x 32 tiles, a warp per tile
+  const int tr = ceil_div(n_row, 32), tc = ceil_div(n_col, 32);
+  for (int q = w; q < tr * tc; q += NW) {
+    const int r0 = (q / tc) * 32, c0 = (q % tc) * 32;
+    for (int k = 0; k < 32; ++k)
+      if (r0 + k < n_row && c0 + lane < n_col) tile[k * 33 + lane] = X[(size_t)(r0 + k) * n_col + c0 + lane];
+    __syncwarp();
+    for (int k = 0; k < 32; ++k)
+      if (c0 + k < n_col && r0 + lane < n_row) XT[(size_t)(c0 + k) * n_row + r0 + lane] = tile[lane * 33 + k];
+    __syncwarp();
+  }
+  grp.sync();
+
+  const int need = min(n_row, n_col);
+  int matched = 0, par = 0;
+  for (int round = 0; matched < need && round < need; ++round) {
+    const int16_t stamp = (int16_t)(round + 1);
+    for (int r = w; r < n_row; r += NW) {
+      int v = rb[r];
+      if (v <= -3) continue;  // matched
+      if (v == -2 || (v >= 0 && cb[v] <= (int16_t)-3)) {
+        float bv;
+        int bi;
+        scan_line(X + (size_t)r * n_col, cb, n_col, lane, bv, bi);
+        v = bi == 0x7fffffff ? -1 : bi;
+        if (lane == 0) rb[r] = (int16_t)v;
+      }
+      if (lane == 0 && v >= 0) tg[v] = stamp;
+    }
+    grp.sync();
+    for (int c = w; c < n_col; c += NW) {
+      if (tg[c] != stamp) continue;  // no live row names it
+      const int v = cb[c];
+      if (!(v == -2 || (v >= 0 && rb[v] <= (int16_t)-3))) continue;
+      float bv;
+      int bi;
+      scan_line(XT + (size_t)c * n_row, rb, n_row, lane, bv, bi);
+      if (lane == 0) cb[c] = bi == 0x7fffffff ? (int16_t)-1 : (int16_t)bi;
+    }
+    grp.sync();
+    int nn = 0;
+    for (int r = t; r < n_row; r += G) {
+      const int c = rb[r];
+      if (c >= 0 && cb[c] == r) {
+        rb[r] = (int16_t)(-3 - c);
+        cb[c] = (int16_t)(-3 - r);
+        ++nn;
+      }
+    }
+    matched += grp.sum_i(nn, par);
+    par ^= 1;
+  }
+  if (matched < need && t == 0 && hdr) set_status(hdr, 6 /* CF_ERR_NUMERIC */, pidx);
+  float sc = 0.f;
+  for (int r = t; r < n_row; r += G) {
+    const int v = rb[r];
+    const int c = v <= -3 ? -3 - v : -1;
+    if (c >= 0) sc += X[(size_t)r * n_col + c];
+    if (mo) mo[r] = c;
+  }
+  return grp.sum(sc, 0);
+}
+
 // Write X_K (resident, possibly transposed, stride ld) to the caller's
 // row-major n_a x n_b output, coalesced on the global side.
 template <class Grp>
@@ -768,6 +877,229 @@ __device__ __forceinline__ void for_entries(int n_row, int n_col, int ld, int t,
   }
 }
 
+// The sweep of one iteration of a global-class pair whose graphs are staged
+// in shared memory.  The entries are cut into strips -- one column j and a
+// run of L consecutive rows -- and team thread t takes strips t, t + G, ...;
+// the lanes of a warp hold consecutive columns of the same rows, so every
+// gather and store is coalesced and the row records are broadcast.  Rows go
+// U at a time: the records, the gathered values and (1 - alpha) Ehat of U
+// rows are all loaded before any of them is used, which keeps U * 9 loads of
+// each thread in flight (the iterates live in L2 or beyond, so a chain of
+// dependent loads per entry would leave the sweep latency-bound).  Rows with
+// further neighbours add those terms in place.  Columns with further
+// neighbours (the STOP block, whose in-degree grows with every early return,
+// and loop exits) are left out: their entries cost many times an ordinary
+// one, so sweep_busy spreads them over the whole team instead of leaving
+// them to the strips' owners.  Returns this thread's partial sum of y^2.
+struct StripPlan {
+  int L, total, rounds;
+};
+
+// S row segments of L rows, S chosen to minimise the entries of the most
+// loaded thread, ceil(S n_col / G) ceil(n_row / S) (ties: fewer segments).
+__device__ __forceinline__ StripPlan strip_plan(int n_row, int n_col, int G) {
+  int bS = 1;
+  long long best = -1;
+  for (int S = 1; S <= 64 && S <= n_row; ++S) {
+    const long long c = (long long)ceil_div(S * n_col, G) * ceil_div(n_row, S);
+    if (best < 0 || c < best) {
+      best = c;
+      bS = S;
+    }
+  }
+  const int L = ceil_div(n_row, bS);
+  const int total = ceil_div(n_row, L) * n_col;
+  return StripPlan{L, total, ceil_div(total, G)};
+}
+
+template <int U>
+__device__ __forceinline__ float sweep_strips(const StripPlan& sp, int t, int G, int n_row, int n_col, int ld,
+                                              const char* cur, float* nxt, const float* ehb, float ca,
+                                              const int4* ra, const int4* rq, const int4* rr, const int2* redge,
+                                              const int2* cedge, const int* cptr) {
+  float ss = 0.f;
+  for (int rd = 0; rd < sp.rounds; ++rd) {
+    const int q = t + rd * G;
+    const int j = q < sp.total ? q % n_col : 0;
+    const ColPad cl = load_col(cptr, cedge, n_col, j);
+    const bool act = q < sp.total && !cl.flag;
+    const int i0 = act ? (q / n_col) * sp.L : 0;
+    const int i1 = act ? min(n_row, i0 + sp.L) : 0;
+    int i = i0;
+    for (; i + U <= i1; i += U) {
+      int4 A[U], Q[U];
+      float z[U], e[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        A[u] = ra[i + u];
+        Q[u] = rq[i + u];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        z[u] = gather_fast(cur, A[u], Q[u], cl);
+        e[u] = ehb[(size_t)(i + u) * ld + j];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (A[u].w < 0) z[u] += row_extra(cur, rr[i + u], redge, cl);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const float y = fmaf(ca, z[u], e[u]);
+        nxt[(size_t)(i + u) * ld + j] = y;
+        ss = fmaf(y, y, ss);
+      }
+    }
+    for (; i < i1; ++i) {
+      const int4 A = ra[i];
+      float z = gather_fast(cur, A, rq[i], cl);
+      if (A.w < 0) z += row_extra(cur, rr[i], redge, cl);
+      const float y = fmaf(ca, z, ehb[(size_t)i * ld + j]);
+      nxt[(size_t)i * ld + j] = y;
+      ss = fmaf(y, y, ss);
+    }
+  }
+  return ss;
+}
+
+// Terms of entry (i, j) from the further neighbours of column j, as
+// col_extra, with each neighbour's loads issued four at a time.
+__device__ __forceinline__ float col_extra_g(const char* Y, const int4 A, const int4 Q, const int4 rr,
+                                             const int2* redge, const int2* cedge, const int* cptr, int n_col,
+                                             int j) {
+  float s = 0.f;
+  const float a0 = fabsf(__int_as_float(A.y)), a1 = fabsf(__int_as_float(A.w));
+  const float q0 = __int_as_float(Q.y), q1 = __int_as_float(Q.w);
+  auto term = [&](int u0, int u1, float w0, float w1, int r0, int r1, int2 v) {
+    float t = fmaf(w1, lds_at(Y, u1, v.x), w0 * lds_at(Y, u0, v.x));
+    for (int k = r0 + 2; k < r1; ++k) {
+      const int2 e = redge[k];
+      t = fmaf(__int_as_float(e.y), lds_at(Y, e.x, v.x), t);
+    }
+    return __int_as_float(v.y) * t;
+  };
+  const int xo0 = cptr[j] + 2, xo1 = cptr[j + 1];
+  const int xi0 = cptr[n_col + 1 + j] + 2, xi1 = cptr[n_col + 2 + j];
+#pragma unroll 4
+  for (int f = xo0; f < xo1; ++f) s += term(A.x, A.z, a0, a1, rr.x, rr.y, cedge[f]);
+#pragma unroll 4
+  for (int f = xi0; f < xi1; ++f) s += term(Q.x, Q.z, q0, q1, rr.z, rr.w, cedge[f]);
+  return s;
+}
+
+// The entries of the columns with further neighbours (nbc of them, listed in
+// bcol), every one computed in full -- first two neighbours, row extras,
+// column extras -- by whichever team thread takes it: items t, t + G, ...
+// of the nbc x n_row of them, consecutive items down a column.
+__device__ __forceinline__ float sweep_busy(int nbc, const int16_t* bcol, int t, int G, int n_row, int n_col, int ld,
+                                            const char* cur, float* nxt, const float* ehb, float ca,
+                                            const int4* ra, const int4* rq, const int4* rr, const int2* redge,
+                                            const int2* cedge, const int* cptr) {
+  float ss = 0.f;
+  const int items = nbc * n_row;
+  for (int k = t; k < items; k += G) {
+    const int b = k / n_row, i = k - b * n_row;
+    const int j = bcol[b];
+    const ColPad cl = load_col(cptr, cedge, n_col, j);
+    const int4 A = ra[i], Q = rq[i], R4 = rr[i];
+    const size_t off = (size_t)i * ld + j;
+    const float e = ehb[off];
+    float z = gather_fast(cur, A, Q, cl);
+    if (A.w < 0) z += row_extra(cur, R4, redge, cl);
+    z += col_extra_g(cur, A, Q, R4, redge, cedge, cptr, n_col, j);
+    const float y = fmaf(ca, z, e);
+    nxt[off] = y;
+    ss = fmaf(y, y, ss);
+  }
+  return ss;
+}
+
+// Busy columns through per-row sums.  For a column j with further
+// neighbours, entry (i, j) of the gathered sum is
+//   sum_{i->u} w_iu S_j[u] + sum_{u->i} w_ui P_j[u],
+//   S_j[u] = sum_{j->v} w_jv Y[u,v],  P_j[u] = sum_{v->j} w_vj Y[u,v],
+// so the many neighbours of such a column (the STOP block collects an edge
+// from every early return) are read once per row u, along that row, instead
+// of once per entry with a stride of one row per lane.  bsum_rows writes the
+// sums into T (n_row rows of kBusySlots floats: slot 2b = S, 2b + 1 = P of
+// busy column b), a warp per row: the column lists are cut into sub-slots of
+// at most eight entries (sub: cedge begin, count | slot << 8), a lane takes
+// sub-slots lane and lane + 32 with their loads all in flight, and each
+// slot's sub-slot partials are then added in table order (slots: first sub,
+// count), so the sums do not depend on timing.  bsum_entries then computes
+// every busy-column entry (nbc x n_row items, consecutive items along a
+// row) from row i's neighbour lists and T.
+constexpr int kBusySlots = 64;  // 2 x up to 32 busy columns
+constexpr int kBusySubs = 64;   // sub-slots: two per lane
+
+__device__ __forceinline__ void bsum_rows(int w, int NW, int lane, int n_row, int ld, const char* cur, int nsub,
+                                          const int2* sub, int nslot, const int* slots, const int2* cedge,
+                                          float* pw, float* T) {
+  for (int u = w; u < n_row; u += NW) {
+    const char* row = cur + (size_t)u * ld * 4;
+    float part[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int si = lane + 32 * h;
+      part[h] = 0.f;
+      if (si < nsub) {
+        const int2 e = sub[si];
+        const int cnt = e.y & 0xff;
+        float v[8], wt[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int2 ce = q < cnt ? cedge[e.x + q] : make_int2(0, 0);
+          wt[q] = __int_as_float(ce.y);
+          v[q] = lds_at(row, 0, ce.x);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) part[h] = fmaf(wt[q], v[q], part[h]);
+      }
+    }
+    pw[lane] = part[0];
+    pw[lane + 32] = part[1];
+    __syncwarp();
+    for (int sl = lane; sl < nslot; sl += 32) {
+      const int f = slots[sl] & 0xffff, c = slots[sl] >> 16;
+      float acc = 0.f;
+      for (int q = 0; q < c; ++q) acc += pw[f + q];
+      T[(size_t)u * kBusySlots + sl] = acc;
+    }
+    __syncwarp();
+  }
+}
+
+__device__ __forceinline__ float bsum_entries(int nbc, const int16_t* bcol, int t, int G, int n_row, int ld,
+                                              float* nxt, const float* ehb, float ca, const int4* ra, const int4* rq,
+                                              const int4* rr, const int2* redge, const float* T) {
+  float ss = 0.f;
+  const unsigned rs = 4u * (unsigned)ld;  // byte stride of a row: row offsets A.x = 4 ld u
+  const int items = nbc * n_row;
+  for (int k = t; k < items; k += G) {
+    const int i = k / nbc, b = k - i * nbc;
+    const int j = bcol[b];
+    const int4 A = ra[i], Q = rq[i], R4 = rr[i];
+    const float* So = T + 2 * b;
+    const float* Pi = T + 2 * b + 1;
+    float z = fabsf(__int_as_float(A.y)) * So[((unsigned)A.x / rs) * kBusySlots] +
+              fabsf(__int_as_float(A.w)) * So[((unsigned)A.z / rs) * kBusySlots] +
+              __int_as_float(Q.y) * Pi[((unsigned)Q.x / rs) * kBusySlots] +
+              __int_as_float(Q.w) * Pi[((unsigned)Q.z / rs) * kBusySlots];
+    for (int q = R4.x + 2; q < R4.y; ++q) {
+      const int2 e = redge[q];
+      z = fmaf(__int_as_float(e.y), So[((unsigned)e.x / rs) * kBusySlots], z);
+    }
+    for (int q = R4.z + 2; q < R4.w; ++q) {
+      const int2 e = redge[q];
+      z = fmaf(__int_as_float(e.y), Pi[((unsigned)e.x / rs) * kBusySlots], z);
+    }
+    const size_t off = (size_t)i * ld + j;
+    const float y = fmaf(ca, z, ehb[off]);
+    nxt[off] = y;
+    ss = fmaf(y, y, ss);
+  }
+  return ss;
+}
+
 // A global-class pair (too large for shared memory) on a team -- the whole
 // CTA, or every CTA of a thread-block cluster: the iterates, (1-alpha) Ehat
 // and the matching state live in a scratch slot of the workspace
@@ -777,7 +1109,7 @@ __device__ __forceinline__ void for_entries(int n_row, int n_col, int ld, int t,
 // row-major order (team rank t takes t, t + G, ...).  Slot: [ehb | buf0 |
 // buf1] (n_row x n_col floats each), row norms, int32 matching state.
 // loc: this CTA (for the staging); team: the threads sharing the pair.
-template <bool kStaged, class Grp>
+template <bool kStaged, int U, class Grp>
 __device__ __noinline__ void run_pair_g(const Ctx& cx, const Geo& g, const Group& loc, const Grp& grp, float* slot,
                                         unsigned char* region) {
   const int n_row = g.na, n_col = g.nb, ld = g.nb;  // global-class shapes are never transposed
@@ -801,7 +1133,9 @@ __device__ __noinline__ void run_pair_g(const Ctx& cx, const Geo& g, const Group
   const int e_col = __ldg(g.c_optr + n_col) - co0;
   int2* cedge = redge + 2 * e_row;
   int* cptr = reinterpret_cast<int*>(cedge + 2 * e_col);
-  for (int i = t; i < n_row; i += G) rn[i] = attr_norm(g.r_attr + (size_t)i * cx.Fp, cx.om, cx.Fp);
+  for (int i = t; i < n_row + n_col; i += G)
+    rn[i] = i < n_row ? attr_norm(g.r_attr + (size_t)i * cx.Fp, cx.om, cx.Fp)
+                      : attr_norm(g.c_attr + (size_t)(i - n_row) * cx.Fp, cx.om, cx.Fp);
   const int lt = loc.rank, LG = loc.size;
   for (int i = lt; kStaged && i < n_row; i += LG) {
     const int o0 = __ldg(g.r_optr + i) - eo0, o1 = __ldg(g.r_optr + i + 1) - eo0;
@@ -828,19 +1162,65 @@ __device__ __noinline__ void run_pair_g(const Ctx& cx, const Geo& g, const Group
     cptr[k] = __ldg(g.c_optr + k) - co0;
     cptr[n_col + 1 + k] = e_col + __ldg(g.c_iptr + k) - ci0;
   }
+  // the columns with further neighbours, in index order (warp 0 of this CTA)
+  int* nbcp = reinterpret_cast<int*>(align_up(reinterpret_cast<size_t>(cptr + 2 * (n_col + 1)), 16));
+  int16_t* bcol = reinterpret_cast<int16_t*>(nbcp + 4);
+  // and, for the busy-column sums, the sub-slot table (lane 0 of warp 0):
+  // nbcp = {busy columns, sub-slots, slots, 0}; 0 sub-slots when the table
+  // does not fit, and sweep_busy then takes those entries directly
+  int2* bsub = reinterpret_cast<int2*>(align_up(reinterpret_cast<size_t>(bcol + n_col), 16));
+  int* bslot = reinterpret_cast<int*>(bsub + kBusySubs);
+  float* bpw = reinterpret_cast<float*>(bslot + kBusySlots) + loc.warp() * kBusySlots;
+  if (kStaged && lt < 32) {
+    int cnt = 0;
+    for (int b = 0; b < n_col; b += 32) {
+      const int j = b + lt;
+      const bool x = j < n_col && (__ldg(g.c_optr + j + 1) - __ldg(g.c_optr + j) > 2 ||
+                                   __ldg(g.c_iptr + j + 1) - __ldg(g.c_iptr + j) > 2);
+      const unsigned msk = __ballot_sync(0xffffffffu, x);
+      if (x) bcol[cnt + __popc(msk & ((1u << lt) - 1u))] = (int16_t)j;
+      cnt += __popc(msk);
+    }
+    __syncwarp();
+    if (lt == 0) {
+      int ns = 0;
+      bool fit = 2 * cnt <= kBusySlots;
+      for (int b = 0; fit && b < cnt; ++b) {
+        const int j = bcol[b];
+        const int r0[2] = {__ldg(g.c_optr + j) - co0, e_col + __ldg(g.c_iptr + j) - ci0};
+        const int r1[2] = {__ldg(g.c_optr + j + 1) - co0, e_col + __ldg(g.c_iptr + j + 1) - ci0};
+        for (int d = 0; fit && d < 2; ++d) {
+          const int first = ns;
+          for (int e = r0[d]; e < r1[d]; e += 8) {
+            if (ns == kBusySubs) {
+              fit = false;
+              break;
+            }
+            bsub[ns++] = make_int2(e, min(8, r1[d] - e) | ((2 * b + d) << 8));
+          }
+          bslot[2 * b + d] = first | ((ns - first) << 16);
+        }
+      }
+      nbcp[0] = cnt;
+      nbcp[1] = fit ? ns : 0;
+      nbcp[2] = 2 * cnt;
+    }
+  }
   grp.sync();  // staged lists (this CTA) and row norms (the team) visible
+  const int nbc = kStaged ? nbcp[0] : 0;
+  const int nsub = kStaged ? nbcp[1] : 0;
+  float* T = reinterpret_cast<float*>(ms + n_row + 2 * n_col);
 
-  // Entries are visited in row-major order, team thread t taking t, t + G,
-  // ...: the team sweeps a narrow band of rows at a time, so the rows its
-  // gathers read (neighbours of the band) stay cache-resident.  (i, j) of the
-  // next entry follow without a division.
+  // The prologue visits entries in row-major order, team thread t taking t,
+  // t + G, ...: the team sweeps a narrow band of rows at a time.  (i, j) of
+  // the next entry follow without a division.  The iterations run by strips
+  // (sweep_strips, sweep_busy).
 
   // a3: E, |E|, Ehat = X_0
   float ss = 0.f;
   for_entries(n_row, n_col, ld, t, G, [&](int i, int j, size_t off) {
     const float* bcol = g.c_attr + (size_t)j * cx.Fp;
-    const float cj = attr_norm(bcol, cx.om, cx.Fp);
-    const float den = rn[i] * cj;
+    const float den = rn[i] * rn[n_row + j];
     const float e = den > 0.f ? attr_dot(g.r_attr + (size_t)i * cx.Fp, bcol, cx.om, cx.Fp) / den : 0.f;
     ehb[off] = e;
     ss = fmaf(e, e, ss);
@@ -857,30 +1237,30 @@ __device__ __noinline__ void run_pair_g(const Ctx& cx, const Geo& g, const Group
   grp.sync();
 
   // a4: K renormalised iterations, one barrier each
+  const StripPlan sp = strip_plan(n_row, n_col, G);
   float sk = 1.f;
   for (int k = 0; k < cx.K; ++k) {
     const char* cur = reinterpret_cast<const char*>((k & 1) ? buf1 : buf0);
     float* nxt = (k & 1) ? buf0 : buf1;
     const float ca = 0.5f * cx.alpha * sk;
-    ss = 0.f;
-    for_entries(n_row, n_col, ld, t, G, [&](int i, int j, size_t off) {
-      float z;
-      if (kStaged) {
-        const ColPad cl = load_col(cptr, cedge, n_col, j);
-        const int4 A = ra[i], Q = rq[i];
-        z = gather_fast(cur, A, Q, cl);
-        if (A.w < 0 || cl.flag) {
-          const int4 R4 = rr[i];
-          if (A.w < 0) z += row_extra(cur, R4, redge, cl);
-          if (cl.flag) z += col_extra(cur, A, Q, R4, redge, cedge, cptr, n_col, j);
-        }
+    if (kStaged) {
+      ss = sweep_strips<U>(sp, t, G, n_row, n_col, ld, cur, nxt, ehb, ca, ra, rq, rr, redge, cedge, cptr);
+      if (nsub > 0) {
+        bsum_rows(grp.warp(), grp.nwarps(), t & 31, n_row, ld, cur, nsub, bsub, nbcp[2], bslot, cedge, bpw, T);
+        grp.sync();  // T complete
+        ss += bsum_entries(nbc, bcol, t, G, n_row, ld, nxt, ehb, ca, ra, rq, rr, redge, T);
       } else {
-        z = gather_g(reinterpret_cast<const float*>(cur), ld, g, i, j);
+        ss += sweep_busy(nbc, bcol, t, G, n_row, n_col, ld, cur, nxt, ehb, ca, ra, rq, rr, redge, cedge, cptr);
       }
-      const float y = fmaf(ca, z, ehb[off]);
-      nxt[off] = y;
-      ss = fmaf(y, y, ss);
-    });
+    } else {
+      ss = 0.f;
+      for_entries(n_row, n_col, ld, t, G, [&](int i, int j, size_t off) {
+        const float z = gather_g(reinterpret_cast<const float*>(cur), ld, g, i, j);
+        const float y = fmaf(ca, z, ehb[off]);
+        nxt[off] = y;
+        ss = fmaf(y, y, ss);
+      });
+    }
     const float yy = grp.sum(ss, (k + 1) & 1);
     sk = cx.norm_mode == 0 ? 1.0f / sqrtf(yy) : 1.f;
   }
@@ -890,17 +1270,27 @@ __device__ __noinline__ void run_pair_g(const Ctx& cx, const Geo& g, const Group
   if (cx.X) store_x(grp, cx, g, Xs, n_col);
   if (cx.scores || cx.match) {
     int32_t* mo = cx.match ? cx.match + cx.m_off[g.p] : nullptr;
-    const float sc = greedy<int32_t>(grp, Xs, n_col, n_row, n_col, 0, ms, ms + n_row, ms + n_row + n_col, mo, cx.hdr, g.p);
+    float sc;
+    if constexpr (kStaged && std::is_same<Grp, Group>::value)  // one CTA: the state in its shared memory
+      sc = greedy_g(grp, Xs, n_row, n_col, ehb, region, mo, cx.hdr, g.p);
+    else
+      sc = greedy<int32_t>(grp, Xs, n_col, n_row, n_col, 0, ms, ms + n_row, ms + n_row + n_col, mo, cx.hdr, g.p);
     if (cx.scores && t == 0) cx.scores[g.p] = sc;
   }
   grp.sync();
 }
 
+// Rows per batch of the global tier's sweep: as many loads in flight as the
+// thread count's register budget holds (128, 80 and 64 registers).
+constexpr int strip_u(int NT) { return NT <= 512 ? 8 : (NT <= 768 ? 4 : 2); }
+
 // Whether a global-class pair's graphs can be staged in the CTA's shared memory.
 __device__ __forceinline__ bool staged_fits(const Geo& g, int region) {
   const int e_row = __ldg(g.r_optr + g.na) - __ldg(g.r_optr);
   const int e_col = __ldg(g.c_optr + g.nb) - __ldg(g.c_optr);
-  return 48 * (size_t)g.na + 16 * (size_t)(e_row + e_col) + 8 * (size_t)(g.nb + 2) <= (size_t)region;
+  return 48 * (size_t)g.na + 16 * (size_t)(e_row + e_col) + 8 * (size_t)(g.nb + 2) + 32 + 2 * (size_t)g.nb + 16 +
+             8 * kBusySubs + 4 * kBusySlots + 32 * 4 * kBusySlots <=
+         (size_t)region;
 }
 
 // Per-CTA setup, done by thread 0 into shared memory (so the pack views do
@@ -1001,9 +1391,9 @@ __global__ void __launch_bounds__(NT, 1) fwd_batched_kernel(CallArgs a, int per_
         {
           const Geo g = make_geo(cx, (int)cx.queue[q], cc);
           if (staged_fits(g, cc.z_cta))
-            run_pair_g<true>(cx, g, cta, cta, slot, smem);
+            run_pair_g<true, strip_u(NT)>(cx, g, cta, cta, slot, smem);
           else
-            run_pair_g<false>(cx, g, cta, cta, slot, smem);
+            run_pair_g<false, 1>(cx, g, cta, cta, slot, smem);
         }
       }
     }
@@ -1055,9 +1445,9 @@ __global__ void __launch_bounds__(NT, 1) fwd_batched_kernel(CallArgs a, int per_
           if (t == 0) set_status(cx.hdr, 2 /* CF_ERR_WORKSPACE */, per_pair);
         } else {
           if (staged_fits(g, cc.z_cta))
-            run_pair_g<true>(cx, g, cta, cta, pslot, smem);
+            run_pair_g<true, strip_u(NT)>(cx, g, cta, cta, pslot, smem);
           else
-            run_pair_g<false>(cx, g, cta, cta, pslot, smem);
+            run_pair_g<false, 1>(cx, g, cta, cta, pslot, smem);
         }
         break;
       }
@@ -1295,9 +1685,9 @@ __global__ void __launch_bounds__(NT, 1) fwd_cluster_kernel(CallArgs a) {
     if (q >= n_gl) break;
     const Geo g = make_geo(cx, (int)cx.queue[q], cc);
     if (staged_fits(g, cc.z_cta))
-      run_pair_g<true>(cx, g, cta, team, slot, smem);
+      run_pair_g<true, strip_u(NT)>(cx, g, cta, team, slot, smem);
     else
-      run_pair_g<false>(cx, g, cta, team, slot, smem);
+      run_pair_g<false, 1>(cx, g, cta, team, slot, smem);
   }
   for (;;) {
     if (rank == 0 && t == 0) st.q = atomicAdd(&cx.hdr->q_next[kClassCluster], 1u);

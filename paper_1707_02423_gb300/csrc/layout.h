@@ -211,7 +211,8 @@ CF_HD Shape classify(int na, int nb, int ea, int eb, const ClassCfg& c, int xa =
 // iterates and Ehat), row/column norms and the int32 matching state.
 CF_HD size_t global_slot_bytes(int na, int nb) {
   size_t e = (size_t)na * nb;
-  return align_up(4 * (3 * e + 2 * (size_t)(na + nb) + 2 * (size_t)na + nb + 64), kAlign);
+  // Ehat, two iterates, norms, matching state, and 64 busy-column sums per row
+  return align_up(4 * (3 * e + 2 * (size_t)(na + nb) + 2 * (size_t)na + nb + 64 + 64 * (size_t)na), kAlign);
 }
 
 // Adjoint checkpoints: X_k is kept for k = 0, S, 2S, ... with S = ceil(sqrt(K)),

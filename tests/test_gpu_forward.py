@@ -276,7 +276,7 @@ def test_workspace_slots_for_pairs_beyond_shared_memory():
     ws = torch.zeros(small.value, dtype=torch.uint8, device=DEV)
     assert _raw_call(pa, d_pairs, len(pairs), om, ws) == 2  # CF_ERR_WORKSPACE: no room for a slot
     # exactly one slot: the large pairs share it one after another
-    slot = 4 * (3 * 300 * 300 + 2 * 600 + 2 * 300 + 300 + 64)
+    slot = 4 * (3 * 300 * 300 + 2 * 600 + 2 * 300 + 300 + 64 + 64 * 300)  # + per-row busy-column sums
     slot = (slot + 255) // 256 * 256
     ws = torch.zeros(small.value + slot, dtype=torch.uint8, device=DEV)
     sc = torch.empty(len(pairs), device=DEV)
@@ -333,4 +333,36 @@ def test_cfg_too_large_to_stage():
     small = [structured_cfg(rng, n, 3, 12) for n in (5, 9)]
     cfgs = [big] + small
     pairs = np.array([(0, 1), (2, 0), (0, 2)], np.int32)
+    compare(cfgs, cfgs, pairs, 13)
+
+
+
+def _with_edges(rng, base, n_hubs, fan, n_fans):
+    """base with `fan` extra in-edges into each of n_hubs random blocks (hub
+    in-degrees about `fan`, like a STOP block reached by many early returns)
+    and two extra out-edges from each of n_fans random blocks."""
+    src, dst, w = [base.src], [base.dst], [base.w]
+    for h in rng.choice(np.arange(1, base.n), n_hubs, replace=False):
+        src.append(rng.choice(base.n - 1, fan, replace=False).astype(np.int32))
+        dst.append(np.full(fan, h, np.int32))
+        w.append(rng.random(fan).astype(np.float32))
+    for s in rng.choice(base.n - 1, n_fans, replace=False):
+        src.append(np.full(2, s, np.int32))
+        dst.append(rng.choice(base.n, 2, replace=False).astype(np.int32))
+        w.append(rng.random(2).astype(np.float32))
+    return CFG(base.n, np.concatenate(src), np.concatenate(dst), np.concatenate(w), base.attr)
+
+
+@pytest.mark.parametrize("n_hubs,fan,n_fans", [(2, 30, 0), (0, 0, 48)])
+def test_global_tier_busy_columns(n_hubs, fan, n_fans):
+    """Global-tier pairs whose column graph has blocks with further
+    neighbours: two hubs of in-degree about 30 (their entries go through
+    per-row sums of the column lists), or more such blocks than the per-row
+    sums hold (their entries are gathered one by one).  700 x 650 blocks:
+    X is beyond any cluster's shared memory."""
+    rng = np.random.default_rng(1000)
+    busy = _with_edges(rng, structured_cfg(rng, 700, 6, 12), n_hubs, fan, n_fans)
+    plain = structured_cfg(rng, 650, 6, 12)
+    cfgs = [busy, plain]
+    pairs = np.array([(1, 0), (0, 1), (0, 0)], np.int32)
     compare(cfgs, cfgs, pairs, 13)
