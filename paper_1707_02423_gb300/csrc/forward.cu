@@ -689,12 +689,6 @@ __device__ __forceinline__ void run_pair_s(const Ctx& cx, const Geo& g, const Gr
   for (int i = t; i < s.n_row; i += grp.size) {
     const int o0 = __ldg(g.r_optr + i) - eo0, o1 = __ldg(g.r_optr + i + 1) - eo0;
     const int q0 = __ldg(g.r_iptr + i) - ei0, q1 = __ldg(g.r_iptr + i + 1) - ei0;
-    const CfAdj z{0, 0.f};
-    const CfAdj a0 = o1 > o0 ? ldg_adj(g.r_oadj + eo0 + o0) : z, a1 = o1 > o0 + 1 ? ldg_adj(g.r_oadj + eo0 + o0 + 1) : z;
-    const CfAdj b0 = q1 > q0 ? ldg_adj(g.r_iadj + ei0 + q0) : z, b1 = q1 > q0 + 1 ? ldg_adj(g.r_iadj + ei0 + q0 + 1) : z;
-    const int flag = (o1 - o0 > 2 || q1 - q0 > 2) ? (int)0x80000000 : 0;
-    ra[i] = make_int4(4 * ld * a0.nbr, __float_as_int(a0.w), 4 * ld * a1.nbr, __float_as_int(a1.w) | flag);
-    rq[i] = make_int4(4 * ld * b0.nbr, __float_as_int(b0.w), 4 * ld * b1.nbr, __float_as_int(b1.w));
     rr[i] = make_int4(o0, o1, e_row + q0, e_row + q1);
   }
   for (int k = t; k < e_row; k += grp.size) {
@@ -730,24 +724,6 @@ __device__ __forceinline__ void run_pair_s(const Ctx& cx, const Geo& g, const Gr
   const int off0 = r0 * ld + j;
   grp.sync();  // staged lists and attribute vectors visible
 
-  // the rows with further neighbours, in index order (warp 0 of the group)
-  if (grp.warp() == 0) {
-    const int lane = t & 31;
-    int cnt = 0;
-    for (int b = 0; b < s.n_row; b += 32) {
-      const int i = b + lane;
-      const bool x = i < s.n_row && ra[i].w < 0;
-      const unsigned msk = __ballot_sync(0xffffffffu, x);
-      if (x) {
-        const int q = cnt + __popc(msk & ((1u << lane) - 1u));
-        brow[2 * q] = (int16_t)i;
-        brow[2 * q + 1] = (int16_t)(i % s.R);
-      }
-      cnt += __popc(msk);
-    }
-    if (lane == 0) *nbusy = cnt;
-  }
-
   // a3: cosine attribute term E, its Frobenius norm, Ehat = X_0
   float ss = 0.f;
   if (staged) {
@@ -782,7 +758,67 @@ __device__ __forceinline__ void run_pair_s(const Ctx& cx, const Geo& g, const Gr
     buf0[off] = eh;
     ehb[off] = cb * eh;
   }
-  grp.sync();  // staged column pointers visible
+  // The order in which each thread's rows are swept (warp 0 of the group,
+  // into the free iterate, which the attribute vectors no longer occupy):
+  // first the rows with at most one out- and one in-neighbour (most blocks
+  // of a CFG), in index order, then the rest.  pos[i] = position of row i.
+  // Also the rows with further neighbours, each with the thread slot
+  // (position mod R) of the threads that sweep it.
+  int16_t* pos = reinterpret_cast<int16_t*>(buf1);
+  if (grp.warp() == 0) {
+    const int lane = t & 31;
+    int na = 0;
+    for (int b = 0; b < s.n_row; b += 32) {
+      const int i = b + lane;
+      int4 e = i < s.n_row ? rr[i] : make_int4(0, 0, 0, 0);
+      const bool x = i < s.n_row && e.y - e.x <= 1 && e.w - e.z <= 1;
+      const unsigned msk = __ballot_sync(0xffffffffu, x);
+      if (x) pos[i] = (int16_t)(na + __popc(msk & ((1u << lane) - 1u)));
+      na += __popc(msk);
+    }
+    int nb = na, cnt = 0;
+    for (int b = 0; b < s.n_row; b += 32) {
+      const int i = b + lane;
+      const int4 e = i < s.n_row ? rr[i] : make_int4(0, 0, 0, 0);
+      const bool x = i < s.n_row && !(e.y - e.x <= 1 && e.w - e.z <= 1);
+      const unsigned msk = __ballot_sync(0xffffffffu, x);
+      const int p = nb + __popc(msk & ((1u << lane) - 1u));
+      if (x) pos[i] = (int16_t)p;
+      nb += __popc(msk);
+      const bool bz = x && (e.y - e.x > 2 || e.w - e.z > 2);
+      const unsigned bm = __ballot_sync(0xffffffffu, bz);
+      if (bz) {
+        const int q = cnt + __popc(bm & ((1u << lane) - 1u));
+        brow[2 * q] = (int16_t)i;
+        brow[2 * q + 1] = (int16_t)(p % s.R);
+      }
+      cnt += __popc(bm);
+    }
+    if (lane == 0) {
+      nbusy[0] = cnt;
+      nbusy[1] = na;
+    }
+  }
+  grp.sync();  // staged column pointers, row order visible
+  // the row records, by position p: ra[p] = {row i | first out-neighbour u
+  // << 16, first in-neighbour u' | flags << 16, w_iu, w_u'i} (bit 16 of the
+  // flags: further neighbours); rq[p] = the second out- and in-neighbours
+  // {u ld 4, w, u' ld 4, w'} (rows past the first group only); missing
+  // neighbours padded with {0, 0}
+  for (int i = t; i < s.n_row; i += grp.size) {
+    const int4 e = rr[i];
+    const int p = pos[i];
+    const int2 z2 = make_int2(0, 0);
+    const int2 a0 = e.y > e.x ? redge[e.x] : z2, a1 = e.y > e.x + 1 ? redge[e.x + 1] : z2;
+    const int2 b0 = e.w > e.z ? redge[e.z] : z2, b1 = e.w > e.z + 1 ? redge[e.z + 1] : z2;
+    const unsigned rs = 4u * (unsigned)ld;
+    const unsigned busy = (e.y - e.x > 2 || e.w - e.z > 2) ? 1u : 0u;
+    ra[p] = make_int4((int)((unsigned)i | (((unsigned)a0.x / rs) << 16)), (int)(((unsigned)b0.x / rs) | (busy << 16)),
+                      a0.y, b0.y);
+    rq[p] = make_int4(a1.x, a1.y, b1.x, b1.y);
+  }
+  const int na_rows = nbusy[1];
+  grp.sync();  // row records visible (pos is overwritten by the first iteration)
   const ColPad cl = load_col(cptr, cedge, s.n_col, j);
 
   // a4: K renormalised iterations, one barrier each.  The main sweep is the
@@ -791,16 +827,39 @@ __device__ __forceinline__ void run_pair_s(const Ctx& cx, const Geo& g, const Gr
   // of busy columns (by the owner's whole warp), and the norm's partial sums
   // are updated by y_new^2 - y_old^2.
   const int nbr = *nbusy;
+  // positions p = r0 + R m: the first m1 of them are rows of the first group
+  const int m1 = (Mt > 0 && na_rows > r0) ? min(Mt, ceil_div(na_rows - r0, s.R)) : 0;
+  const int ld4 = 4 * ld;
   float sk = 1.f;
   for (int k = 0; k < cx.K; ++k) {
     const char* cur = reinterpret_cast<const char*>((k & 1) ? buf1 : buf0);
     float* nxt = (k & 1) ? buf0 : buf1;
     const float ca = 0.5f * cx.alpha * sk;
     ss = 0.f;
-#pragma unroll 2
-    for (int m = 0, i = r0, off = off0; m < Mt; ++m, i += s.R, off += step) {
-      const int4 A = ra[i], Q = rq[i];
-      const float y = fmaf(ca, gather_fast(cur, A, Q, cl), ehb[off]);
+    // rows with at most one out- and one in-neighbour: four loads
+#pragma unroll 1
+    for (int m = 0, p = r0; m < m1; ++m, p += s.R) {
+      const int4 A = ra[p];
+      const int i = A.x & 0xffff;
+      const int uo = ((unsigned)A.x >> 16) * ld4, ui = (A.y & 0xffff) * ld4;
+      const float a0 = lds_at(cur, uo, cl.vo0), a1 = lds_at(cur, uo, cl.vo1);
+      const float b0 = lds_at(cur, ui, cl.vi0), b1 = lds_at(cur, ui, cl.vi1);
+      const float so = __int_as_float(A.z) * fmaf(cl.wo1, a1, cl.wo0 * a0);
+      const float si = __int_as_float(A.w) * fmaf(cl.wi1, b1, cl.wi0 * b0);
+      const int off = i * ld + j;
+      const float y = fmaf(ca, so + si, ehb[off]);
+      nxt[off] = y;
+      ss = fmaf(y, y, ss);
+    }
+    // the other rows: the straight-line 2 x 2 gather (eight loads)
+#pragma unroll 1
+    for (int m = m1, p = r0 + m1 * s.R; m < Mt; ++m, p += s.R) {
+      const int4 A = ra[p], B2 = rq[p];
+      const int i = A.x & 0xffff;
+      const int4 Ao = make_int4(((unsigned)A.x >> 16) * ld4, A.z, B2.x, B2.y);
+      const int4 Qi = make_int4((A.y & 0xffff) * ld4, A.w, B2.z, B2.w);
+      const int off = i * ld + j;
+      const float y = fmaf(ca, gather_fast(cur, Ao, Qi, cl), ehb[off]);
       nxt[off] = y;
       ss = fmaf(y, y, ss);
     }
@@ -818,12 +877,18 @@ __device__ __forceinline__ void run_pair_s(const Ctx& cx, const Geo& g, const Gr
     __syncwarp();
     for (unsigned bm = __ballot_sync(0xffffffffu, cl.flag && Mt > 0); bm; bm &= bm - 1) {
       const int bl = __ffs(bm) - 1;
-      const int jb = __shfl_sync(0xffffffffu, j, bl), ib = __shfl_sync(0xffffffffu, r0, bl);
+      const int jb = __shfl_sync(0xffffffffu, j, bl), pb = __shfl_sync(0xffffffffu, r0, bl);
       const int mb = __shfl_sync(0xffffffffu, Mt, bl);
       for (int m = t & 31; m < mb; m += 32) {
-        const int i = ib + m * s.R, off = i * ld + jb;
+        const int p = pb + m * s.R;
+        const int4 A = ra[p], B2 = rq[p];
+        const bool two = p >= na_rows;
+        const int i = A.x & 0xffff;
+        const int4 Ao = make_int4(((unsigned)A.x >> 16) * ld4, A.z, two ? B2.x : 0, two ? B2.y : 0);
+        const int4 Qi = make_int4((A.y & 0xffff) * ld4, A.w, two ? B2.z : 0, two ? B2.w : 0);
+        const int off = i * ld + jb;
         const float y0 = nxt[off];
-        const float y = fmaf(ca, col_extra(cur, ra[i], rq[i], rr[i], redge, cedge, cptr, s.n_col, jb), y0);
+        const float y = fmaf(ca, col_extra(cur, Ao, Qi, rr[i], redge, cedge, cptr, s.n_col, jb), y0);
         nxt[off] = y;
         ss += y * y - y0 * y0;
       }
