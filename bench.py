@@ -191,7 +191,7 @@ def make_fwd_bwd(w, dev, tune_cache=None, bwd_tune=0):
     out = {"scores": torch.empty(P, dtype=torch.float32, device=dev),
            "match": torch.empty(int(m_off[-1]), dtype=torch.int32, device=dev)}
     tune = pick_tune(pa, pb, pairs_np, omega, tune_cache)
-    ws_bytes = api.ws_size(pa, pb, pairs_np, prm)
+    ws_bytes = api.ws_size(pa, pb, pairs_np, B.params(ALPHA, K_ITERS, tune=tune))
     g = torch.ones(P, dtype=torch.float32, device=dev)
     grads = {"grad_w_a": torch.zeros(int(pa.info.n_user_edges), dtype=torch.float32, device=dev),
              "grad_omega": torch.zeros(w.F, dtype=torch.float32, device=dev)}
@@ -506,7 +506,8 @@ def make_step(name, dev, tune_cache=None, bwd_tune=0):
     # kernels per forward call: the three plan kernels, the persistent forward
     # and, under a cluster tune, the cluster-tier kernel; per adjoint call: the
     # three plan kernels, the accumulator reset, the adjoint and the scatter
-    n_fwd = 4 + (1 if api.tune_info(tune)["cluster"] >= 2 else 0)
+    n_fwd = 4 + (1 if api.tune_info(tune)["cluster"] >= 2 else 0) + \
+        (1 if api.tune_info(tune)["matching"].startswith("ranked, sequential") else 0)
     n_bwd = 3 + 1 + 2 + (1 if w.shared else 2)  # plan, zero, large-pair and resident kernels, scatter
     if name == "dist":  # the C ABI directly, every buffer allocated before the timed region
         L = B.lib()
@@ -549,7 +550,7 @@ def make_step(name, dev, tune_cache=None, bwd_tune=0):
                               wws.data_ptr(), wws.numel(), st))
         return step, 1, 4, tune
     if name in ("cfg2", "cfg3"):
-        ws_bytes = api.ws_size(pa, pb, pairs_np, prm)
+        ws_bytes = api.ws_size(pa, pb, pairs_np, B.params(ALPHA, K_ITERS, tune=tune))
 
         def step():
             api.similarity(pa, pb, pairs_np, omega, ALPHA, K_ITERS, want_match=True, ws=ws, d_pairs=d_pairs,
@@ -608,7 +609,8 @@ def make_query_step(w, pa, pb, omega, d_pairs, ws, tune):
     g = api.Graph(dev)
     with g.capture():
         body()
-    n_fwd = 4 + (1 if api.tune_info(tune)["cluster"] >= 2 else 0)
+    n_fwd = 4 + (1 if api.tune_info(tune)["cluster"] >= 2 else 0) + \
+        (1 if api.tune_info(tune)["matching"].startswith("ranked, sequential") else 0)
 
     def replay():
         g.launch()
@@ -748,7 +750,6 @@ def run_ours(args):
     d_pairs = torch.from_numpy(pairs_np).to(dev)
     ws = api.Workspace(dev)
     prm = B.params(ALPHA, K_ITERS)
-    ws_bytes = api.ws_size(pack, pack, pairs_np, prm)
     x_off, m_off = api.out_offsets(pack, pack, pairs_np)
     out = {"scores": torch.empty(P, dtype=torch.float32, device=dev),
            "match": torch.empty(int(m_off[-1]), dtype=torch.int32, device=dev)}
@@ -763,6 +764,9 @@ def run_ours(args):
         tune = FIXED_TUNE
     else:
         tune, tune_ms = api.autotune(pack, pack, pairs_np, omega, ALPHA, K_ITERS, cache_path=args.tune_cache)
+    prm.tune = tune
+    ws_bytes = api.ws_size(pack, pack, pairs_np, prm)  # with room for deferred matching steps under such a tune
+    deferred = api.tune_info(tune)["matching"].startswith("ranked, sequential")
 
     def sim(flags):
         api.similarity(pack, pack, pairs_np, omega, ALPHA, K_ITERS, want_match=True, ws=ws, d_pairs=d_pairs,
@@ -848,7 +852,6 @@ def run_ours(args):
     # pack from the host CFG arrays, upload the pairs from pinned memory,
     # compute, read scores and matchings back into pinned memory
     L = B.lib()
-    prm.tune = tune
     pairs_pin = torch.from_numpy(pairs_np).pin_memory()
     sc_pin = torch.empty(P, dtype=torch.float32).pin_memory()
     mt_pin = torch.empty(int(m_off[-1]), dtype=torch.int32).pin_memory()
@@ -914,7 +917,9 @@ def run_ours(args):
                    "step": "two CUDA-graph launches: plan (workspace reset + 3 kernels), forward (queue reset + "
                            "persistent kernel); sum of per-step CUDA events",
                    "tune": {**api.tune_info(tune), "autotune_sample_ms": tune_ms}},
-        "roofline": {"bound": "smem", "kernel": "fwd_batched_kernel", "achieved": achieved,
+        "roofline": {"bound": "smem",
+                     "kernel": "fwd_batched_kernel + match_deferred_kernel (the forward graph)" if deferred
+                     else "fwd_batched_kernel", "achieved": achieved,
                      "peak": smem_peak_gbs, "unit": "GB/s", "frac": achieved / smem_peak_gbs,
                      "traffic": traffic,
                      "peak_source": f"of measured: cf_probe shared-memory loads {smem_probe['per_clk_sm']:.1f} "
@@ -946,9 +951,10 @@ def run_ours(args):
                 "ms_per_step": e2e_s * 1e3,
                 "what": "cf_pack_cfgs (host build + copy) + pinned pair upload + cf_similarity + pinned "
                         "readback of scores and matchings, wall clock"},
-        # per step: the three plan kernels, the persistent forward, and the
-        # cluster-tier kernel when the tune has one
-        "gpu_launches": (4 + (1 if api.tune_info(tune)["cluster"] >= 2 else 0)) * args.steps,
+        # per step: the three plan kernels, the persistent forward, the
+        # cluster-tier kernel when the tune has one, and the deferred
+        # matching steps when the tune defers them
+        "gpu_launches": (4 + (1 if api.tune_info(tune)["cluster"] >= 2 else 0) + (1 if deferred else 0)) * args.steps,
         "clocks": clk,
         "probes": probes,
         "wall_s_timed_region": t_wall,

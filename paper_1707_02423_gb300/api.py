@@ -189,7 +189,8 @@ def tune_info(tune: int) -> dict:
     r = B.cf_tune_info()
     B.check(B.lib().cf_tune_describe(int(tune), C.byref(r)))
     return {"tune": r.tune, "threads_per_cta": r.threads_per_cta, "smallest_group": r.smallest_group,
-            "matching": ("ranked", "ranked in groups of at most a quarter CTA", "rescans")[r.matching], "cluster": r.cluster}
+            "matching": ("ranked", "ranked in groups of at most a quarter CTA", "rescans",
+                         "ranked, sequential steps in a second kernel")[r.matching], "cluster": r.cluster}
 
 
 def match(pa: Pack, pb: Pack, pairs, X: torch.Tensor, *, ws: Workspace | None = None, stream=None,

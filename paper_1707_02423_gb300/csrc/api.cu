@@ -316,6 +316,14 @@ Tune decode_tune(int32_t id) {
   static const int kClusters[4] = {0, 2, 4, 8};
   const int idx = id >= 1 && id <= kNumTunes ? id - 1 : 0;
   Tune t;
+  if (idx >= kFirstDeferTune - 1) {  // matching policy 3: variant x smallest group x cluster size
+    const int j = idx - (kFirstDeferTune - 1);
+    t.variant = j % 3;
+    t.min_cls = kClassWarp - (j / 3) % 5;
+    t.ranked = 3;
+    t.cluster = kClusters[j / 15];
+    return t;
+  }
   t.variant = idx % 3;
   t.min_cls = kClassWarp - (idx / 3) % 5;
   t.ranked = (idx / 15) % 3;
@@ -478,8 +486,8 @@ cf_status cf_similarity_ws_size(const void* h_pack_a, const void* h_pack_b, cons
     if (s) return s;
   }
   size_t need = 0;
-  int64_t ng = 0;
-  cf_status s = scan_pairs(h_pack_a, h_pack_b, h_pairs, P, nullptr, nullptr, &need, &ng);
+  int64_t ng = 0, xs = 0;
+  cf_status s = scan_pairs(h_pack_a, h_pack_b, h_pairs, P, &xs, nullptr, &need, &ng);
   if (s) return s;
   // scratch slots for global-class pairs: one per concurrently working CTA
   // (the plain form spread over streams: one per stream)
@@ -487,6 +495,9 @@ cf_status cf_similarity_ws_size(const void* h_pack_a, const void* h_pack_b, cons
   int64_t slots = std::min<int64_t>(ng, 2 * (sms > 0 ? sms : 152));
   if (params && (params->flags & CF_FLAG_PER_PAIR_STREAMS) && ng > 0) slots = std::max<int64_t>(slots, kPerPairStreams);
   *bytes = ws_layout(P).fixed_bytes + (size_t)slots * need;
+  // matching policy 3: room for every pair's ranked lists (deferred steps)
+  if (params && decode_tune(params->tune).ranked == 3 && !(params->flags & CF_FLAG_PER_PAIR_LAUNCH))
+    *bytes += defer_bytes(P, xs);
   return ok();
 }
 
@@ -515,6 +526,8 @@ cf_status cf_similarity(const void* d_pack_a, const void* d_pack_b, const int32_
     // only the queue cursors restart; the plan and the status word stay
     e = cudaMemsetAsync(static_cast<char*>(d_ws) + offsetof(WsHeader, q_next), 0, sizeof(uint32_t) * kNumClasses, st);
     if (e != cudaSuccess) return cuda_fail(e, "queue reset");
+    e = cudaMemsetAsync(static_cast<char*>(d_ws) + offsetof(WsHeader, n_def), 0, 2 * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return cuda_fail(e, "queue reset");
   } else {
     NvtxRange nv("cfsim/plan");
     e = cudaMemsetAsync(d_ws, 0, sizeof(WsHeader), st);
@@ -526,6 +539,10 @@ cf_status cf_similarity(const void* d_pack_a, const void* d_pack_b, const int32_
     NvtxRange nv("cfsim/iterate");
     e = launch_forward(a, tn.variant, (params->flags & CF_FLAG_PER_PAIR_LAUNCH) != 0, st);
     if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+    if (tn.ranked == 3 && (a.scores || a.match)) {  // the deferred steps (a no-op if the plan found no room)
+      e = launch_match_deferred(a, st);
+      if (e != cudaSuccess) return cuda_fail(e, "deferred matching launch");
+    }
     if (optimal) {
       if (params->flags & CF_FLAG_REUSE_PLAN) {
         e = cudaMemsetAsync(static_cast<char*>(d_ws) + offsetof(WsHeader, q_opt), 0, sizeof(uint64_t), st);
@@ -692,6 +709,8 @@ cf_status cf_similarity_ws_size_any(const void* h_pack_a, const void* h_pack_b, 
   const int sms = device_sm_count();
   const int64_t slots = std::min<int64_t>(P, 2 * (sms > 0 ? sms : 152));
   *bytes = ws_layout(P).fixed_bytes + (size_t)slots * global_slot_bytes(ha.max_blocks, hb.max_blocks);
+  if (params && decode_tune(params->tune).ranked == 3 && !(params->flags & CF_FLAG_PER_PAIR_LAUNCH))
+    *bytes += defer_bytes(P, (int64_t)P * ha.max_blocks * hb.max_blocks);
   return ok();
 }
 

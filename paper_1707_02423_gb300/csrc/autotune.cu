@@ -75,9 +75,15 @@ struct TuneLayout {
 cf_status tune_layout(const void* h_pack_a, const void* h_pack_b, const std::vector<int32_t>& sp,
                       const cf_params* params, TuneLayout* L) {
   const int S = (int)(sp.size() / 2);
-  size_t ws = 0;
+  size_t ws = 0, ws3 = 0;
   cf_status s = cf_similarity_ws_size(h_pack_a, h_pack_b, sp.data(), S, params, &ws);
   if (s) return s;
+  cf_params p3 = *params;  // the candidates with deferred matching steps need room for the ranked lists
+  p3.flags = 0;
+  p3.tune = kFirstDeferTune;
+  s = cf_similarity_ws_size(h_pack_a, h_pack_b, sp.data(), S, &p3, &ws3);
+  if (s) return s;
+  ws = std::max(ws, ws3);
   int64_t m_elems = 0;
   s = cf_out_sizes(h_pack_a, h_pack_b, sp.data(), S, nullptr, &m_elems);
   if (s) return s;

@@ -60,6 +60,11 @@ struct Ctx {
   const float* sqom;  // sqrt(omega), shared-memory copy
   int F, Fp;
   int ranked;  // matching policy (ClassCfg::ranked)
+  // matching policy 3 with room in the workspace: where the ranked lists of
+  // each pair go (at x_off[p]) and the list of deferred pairs
+  int16_t* def_rk;
+  uint32_t* def_rkey;
+  uint32_t* def_list;
 };
 
 // One pair, oriented: the row graph indexes rows of the resident matrix.
@@ -462,7 +467,8 @@ __device__ __noinline__ float greedy_seq_steps(int lane, bool swap, int nl, int 
 }
 
 __device__ __forceinline__ float greedy_seq(const Group& grp, float* X, int ld, int n_row, int n_col, int tr,
-                                            uint32_t* key, uint32_t* rkey, int32_t* mo, WsHeader* hdr, int pidx) {
+                                            uint32_t* key, uint32_t* rkey, int32_t* mo, WsHeader* hdr, int pidx,
+                                            bool steps = true) {
   const int t = grp.rank, G = grp.size;
   const bool rows = n_col <= n_row;
   const int nl = rows ? n_row : n_col, len = rows ? n_col : n_row;
@@ -495,7 +501,7 @@ __device__ __forceinline__ float greedy_seq(const Group& grp, float* X, int ld, 
   for (int e = t; e < len; e += G) dead[e] = 0;
   grp.sync();
   float sc = 0.f;
-  if (t < 32) {
+  if (steps && t < 32) {
     const bool swap = rows == (tr != 0);
     const int Rn = (nl + 31) >> 5;
     if (Rn <= 1)
@@ -905,8 +911,22 @@ __device__ __forceinline__ void run_pair_s(const Ctx& cx, const Geo& g, const Gr
   if (cx.X) store_x(grp, cx, g, Xs, ld);
   if (cx.scores || cx.match) {
     int32_t* mo = cx.match ? cx.match + cx.m_off[g.p] : nullptr;
-    const bool ranked = cx.ranked == 0 || (cx.ranked == 1 && 4 * grp.size <= (int)blockDim.x);
-    if (ranked && max(s.n_row, s.n_col) <= kSeqMaxLists) {
+    const bool ranked = cx.ranked == 0 || cx.ranked == 3 || (cx.ranked == 1 && 4 * grp.size <= (int)blockDim.x);
+    if (cx.def_rk && max(s.n_row, s.n_col) <= kSeqMaxLists) {
+      // ranked lists here, then copied out for the deferred steps
+      greedy_seq(grp, Xs, ld, s.n_row, s.n_col, s.tr, reinterpret_cast<uint32_t*>(freeb),
+                 reinterpret_cast<uint32_t*>(ehb), mo, cx.hdr, g.p, false);
+      const int E = s.n_row * s.n_col;
+      const int16_t* rk = reinterpret_cast<const int16_t*>(Xs);
+      const uint32_t* rkey = reinterpret_cast<const uint32_t*>(ehb);
+      int16_t* grk = cx.def_rk + cx.x_off[g.p];
+      uint32_t* grkey = cx.def_rkey + cx.x_off[g.p];
+      for (int idx = t; idx < E; idx += grp.size) {
+        grk[idx] = rk[idx];
+        grkey[idx] = rkey[idx];
+      }
+      if (t == 0) cx.def_list[atomicAdd(&cx.hdr->n_def, 1u)] = (uint32_t)g.p | ((uint32_t)s.tr << 31);
+    } else if (ranked && max(s.n_row, s.n_col) <= kSeqMaxLists) {
       // keys in the free iterate, ranked elements over X_K, their keys over Ehat
       const float sc = greedy_seq(grp, Xs, ld, s.n_row, s.n_col, s.tr, reinterpret_cast<uint32_t*>(freeb),
                                   reinterpret_cast<uint32_t*>(ehb), mo, cx.hdr, g.p);
@@ -1372,6 +1392,18 @@ __device__ __forceinline__ bool make_ctx(const CallArgs& a, float* s_om, Ctx& cx
     cx.m_off = reinterpret_cast<const int64_t*>(a.ws + L.m_off);
     cx.scratch = a.ws + L.scratch;
     cx.scratch_bytes = a.ws_bytes > L.scratch ? a.ws_bytes - L.scratch : 0;
+    cx.def_rk = nullptr;
+    cx.def_rkey = nullptr;
+    cx.def_list = nullptr;
+    if (cx.hdr->defer) {  // the scratch slots end where the deferred-steps area starts
+      const uint64_t off = cx.hdr->defer_off;
+      const int64_t xt = cx.hdr->x_total;
+      cx.scratch_bytes = off > L.scratch ? off - L.scratch : 0;
+      cx.def_rk = reinterpret_cast<int16_t*>(a.ws + off);
+      cx.def_rkey = reinterpret_cast<uint32_t*>(a.ws + off + align_up(2 * (size_t)xt, kAlign));
+      cx.def_list = reinterpret_cast<uint32_t*>(a.ws + off + align_up(2 * (size_t)xt, kAlign) +
+                                                align_up(4 * (size_t)xt, kAlign));
+    }
     cx.pairs = a.pairs;
     cx.alpha = a.alpha;
     cx.K = a.K;
@@ -1765,6 +1797,71 @@ __global__ void __launch_bounds__(NT, 1) fwd_cluster_kernel(CallArgs a) {
   }
 }
 
+// The deferred sequential steps of the greedy matching (matching policy 3).
+// The forward ranked each resident pair's lists in its group and left them
+// in the workspace (pair p's at x_off[p]), initialised its matching to -1 and
+// listed the pair (index | orientation << 31); here every warp takes listed
+// pairs one after another and runs the steps of greedy_seq on them, so that
+// a group of the forward is not held by one warp's chain of steps.  The dead
+// flags live in the warp's shared memory.
+constexpr int kDefNT = 256;
+
+__global__ void __launch_bounds__(kDefNT) match_deferred_kernel(CallArgs a) {
+  __shared__ unsigned char s_dead[kDefNT / 32][kSeqMaxLists];
+  __shared__ PackView sA, sB;
+  const WsLayout L = ws_layout(a.P);
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(a.ws + L.hdr);
+  if (!hdr->defer) return;  // the forward matched every pair itself
+  if (threadIdx.x == 0) {
+    sA = load_pack(a.pack_a);
+    sB = load_pack(a.pack_b);
+  }
+  __syncthreads();
+  const uint64_t off = hdr->defer_off;
+  const int64_t xt = hdr->x_total;
+  const int16_t* def_rk = reinterpret_cast<const int16_t*>(a.ws + off);
+  const uint32_t* def_rkey = reinterpret_cast<const uint32_t*>(a.ws + off + align_up(2 * (size_t)xt, kAlign));
+  const uint32_t* def_list = reinterpret_cast<const uint32_t*>(a.ws + off + align_up(2 * (size_t)xt, kAlign) +
+                                                               align_up(4 * (size_t)xt, kAlign));
+  const int64_t* x_off = reinterpret_cast<const int64_t*>(a.ws + L.x_off);
+  const int64_t* m_off = reinterpret_cast<const int64_t*>(a.ws + L.m_off);
+  const uint32_t n = hdr->n_def;
+  const int lane = threadIdx.x & 31;
+  unsigned char* dead = s_dead[threadIdx.x >> 5];
+  for (;;) {
+    uint32_t q = 0;
+    if (lane == 0) q = atomicAdd(&hdr->q_def, 1u);
+    q = __shfl_sync(0xffffffffu, q, 0);
+    if (q >= n) break;
+    const uint32_t ent = def_list[q];
+    const int p = (int)(ent & 0x7fffffffu), tr = (int)(ent >> 31);
+    const int pa = __ldg(a.pairs + 2 * p), pb = __ldg(a.pairs + 2 * p + 1);
+    const int na = __ldg(sA.node_off + pa + 1) - __ldg(sA.node_off + pa);
+    const int nb = __ldg(sB.node_off + pb + 1) - __ldg(sB.node_off + pb);
+    const int n_row = tr ? nb : na, n_col = tr ? na : nb;
+    const bool rows = n_col <= n_row;
+    const int nl = rows ? n_row : n_col, len = rows ? n_col : n_row;
+    const bool swap = rows == (tr != 0);
+    for (int e = lane; e < len; e += 32) dead[e] = 0;
+    __syncwarp();
+    const int16_t* rk = def_rk + x_off[p];
+    const uint32_t* rkey = def_rkey + x_off[p];
+    int32_t* mo = a.match ? a.match + m_off[p] : nullptr;
+    const int Rn = (nl + 31) >> 5;
+    float sc;
+    if (Rn <= 1)
+      sc = greedy_seq_steps<1>(lane, swap, nl, len, rk, rkey, dead, mo, hdr, p);
+    else if (Rn <= 2)
+      sc = greedy_seq_steps<2>(lane, swap, nl, len, rk, rkey, dead, mo, hdr, p);
+    else if (Rn <= 4)
+      sc = greedy_seq_steps<4>(lane, swap, nl, len, rk, rkey, dead, mo, hdr, p);
+    else
+      sc = greedy_seq_steps<8>(lane, swap, nl, len, rk, rkey, dead, mo, hdr, p);
+    if (a.scores && lane == 0) a.scores[p] = sc;
+    __syncwarp();
+  }
+}
+
 // cf_match on caller-given matrices: one CTA per pair, matching state in
 // shared memory (int16, up to kMaxBlocks rows and columns).
 constexpr int kMatchNT = 512;
@@ -1954,6 +2051,16 @@ cudaError_t launch_forward(const CallArgs& a, int variant, bool per_pair, cudaSt
   return variant == 1   ? launch_fwd<512>(a, per_pair, s)
          : variant == 2 ? launch_fwd<768>(a, per_pair, s)
                         : launch_fwd<1024>(a, per_pair, s);
+}
+
+cudaError_t launch_match_deferred(const CallArgs& a, cudaStream_t s) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int g = 4 * sm_count_of(dev);  // 32 warps per SM
+  if (g <= 0) g = 4 * 152;
+  if (a.P > 0) match_deferred_kernel<<<g, kDefNT, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_match_only(const CallArgs& a, cudaStream_t s) {

@@ -50,8 +50,11 @@ ClassCfg fwd_class_cfg(int v, int min_cls, int ranked, int cluster);
 // C if clusters of C CTAs of variant v can be resident on this device, else 0.
 int cluster_supported(int v, int C);
 
-// Kernel configuration selected by cf_params.tune (see decode_tune).
-constexpr int kNumTunes = 180;
+// Kernel configuration selected by cf_params.tune (see decode_tune): ids
+// 1..180 enumerate variant x smallest group x matching policies 0-2 x cluster
+// size, ids 181..240 the same with matching policy 3 (deferred steps).
+constexpr int kNumTunes = 240;
+constexpr int kFirstDeferTune = 181;
 struct Tune {
   int variant, min_cls, ranked, cluster;
 };
@@ -63,6 +66,10 @@ cudaError_t launch_plan(const CallArgs& a, const ClassCfg& cc, cudaStream_t s);
 
 // a2-a6: the batched persistent forward (or one launch per pair).
 cudaError_t launch_forward(const CallArgs& a, int variant, bool per_pair, cudaStream_t s);
+
+// The deferred sequential steps of the greedy matching (matching policy 3):
+// one warp per pair whose ranked lists the forward left in the workspace.
+cudaError_t launch_match_deferred(const CallArgs& a, cudaStream_t s);
 
 // Greedy matching + score on caller-given matrices.
 cudaError_t launch_match_only(const CallArgs& a, cudaStream_t s);

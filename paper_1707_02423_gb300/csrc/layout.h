@@ -80,7 +80,9 @@ struct ClassCfg {
   int min_cls;  // smallest group level pairs may go to (kClassWarp: all levels)
   int ranked;   // matching of resident pairs: 0 ranked lists wherever their
                 // state fits, 1 only in groups of at most a quarter CTA,
-                // 2 never (rescans)
+                // 2 never (rescans), 3 ranked lists wherever their state fits
+                // with the sequential steps deferred to a second kernel
+                // (one warp per pair) when the workspace has room
   int cluster;  // CTAs per cluster of the cluster tier (0: no cluster tier)
   int bwd;      // 1: size regions for the adjoint (bwd_resident_bytes), 0: the forward
 };
@@ -289,7 +291,20 @@ struct WsHeader {
   uint32_t hist[kNumClasses][kBuckets];
   uint32_t cursor[kNumClasses][kBuckets];
   int64_t x_total, m_total;
+  // deferred matching steps (matching policy 3): whether the plan found room
+  // for the ranked lists, the byte offset of that area in the workspace, the
+  // pairs deferred so far and the second kernel's work counter
+  uint32_t defer, n_def, q_def, pad_;
+  uint64_t defer_off;
 };
+
+// Bytes of the deferred-steps area for P pairs with x_total entries in all:
+// every pair's ranked elements (int16) and ranked keys (uint32), the list of
+// deferred pairs (uint32 each), and slack for aligning the area's start.
+CF_HD size_t defer_bytes(int P, int64_t x_total) {
+  return align_up(2 * (size_t)x_total, kAlign) + align_up(4 * (size_t)x_total, kAlign) +
+         align_up(4 * (size_t)(P > 0 ? P : 1), kAlign) + kAlign;
+}
 
 // Byte offsets of the forward workspace sections for P pairs.
 struct WsLayout {

@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_count_kernel(CallArgs a, Cl
   }
 }
 
-__global__ void __launch_bounds__(kPlanThreads) plan_scan_kernel(CallArgs a) {
+__global__ void __launch_bounds__(kPlanThreads) plan_scan_kernel(CallArgs a, int ranked) {
   PlanCtx c = plan_ctx(a);
   if (threadIdx.x == 0) {
     // queue order: class by class; within a class, costliest bucket first
@@ -178,6 +178,19 @@ __global__ void __launch_bounds__(kPlanThreads) plan_scan_kernel(CallArgs a) {
     c.hdr->m_total = tm;
     c.x_off[c.P] = tx;
     c.m_off[c.P] = tm;
+    // matching policy 3: the deferred-steps area at the end of the
+    // workspace, if it fits beside one scratch slot (when any pair needs one)
+    if (ranked == 3) {
+      const WsLayout L = ws_layout(c.P);
+      const size_t need = defer_bytes(c.P, tx);
+      const size_t avail = a.ws_bytes > L.scratch ? a.ws_bytes - L.scratch : 0;
+      const size_t slot =
+          c.hdr->n_class[kClassGlobal] + c.hdr->n_class[kClassCluster] > 0 ? (size_t)c.hdr->slot_need : 0;
+      if (need + slot <= avail) {
+        c.hdr->defer = 1;
+        c.hdr->defer_off = (a.ws_bytes - need + kAlign - 1) / kAlign * kAlign;
+      }
+    }
   }
 }
 
@@ -207,7 +220,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_scatter_kernel(CallArgs a, 
 cudaError_t launch_plan(const CallArgs& a, const ClassCfg& cc, cudaStream_t s) {
   WsLayout L = ws_layout(a.P);
   plan_count_kernel<<<L.plan_blocks, kPlanThreads, 0, s>>>(a, cc);
-  plan_scan_kernel<<<1, kPlanThreads, 0, s>>>(a);
+  plan_scan_kernel<<<1, kPlanThreads, 0, s>>>(a, cc.ranked);
   plan_scatter_kernel<<<L.plan_blocks, kPlanThreads, 0, s>>>(a, cc);
   return cudaGetLastError();
 }

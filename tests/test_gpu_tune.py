@@ -34,7 +34,8 @@ def wl():
     return w, pa, torch.tensor(om, dtype=torch.float32, device=DEV), ref
 
 
-NT = 180
+NT = 240
+DEFER = [181, 182, 183, 198, 228]  # matching steps deferred: 1024 / 512 / 768 threads; 768 with 2- and 8-CTA clusters
 
 
 def test_tune_table():
@@ -52,7 +53,8 @@ def test_tune_table():
     assert api.tune_info(0) == {**api.tune_info(1), "tune": 0}
 
 
-@pytest.mark.parametrize("tune", list(range(1, NT + 1, 7)) + [2, 3, 6, 9, 12, 15, 45, 46, 47, 90, 92, 135, 136, 180])
+@pytest.mark.parametrize("tune", list(range(1, NT + 1, 7)) + [2, 3, 6, 9, 12, 15, 45, 46, 47, 90, 92, 135, 136, 180]
+                         + DEFER)
 def test_every_tune_matches_oracle(wl, tune):
     w, pa, om, ref = wl
     res = api.similarity(pa, pa, w.pairs, om, 0.8, 40, want_match=True, tune=tune)
@@ -90,3 +92,52 @@ def test_autotune_picks_a_tune_and_caches_it(wl, tmp_path):
     r0 = api.similarity(pa, pa, w.pairs, om, want_match=True)
     r1 = api.similarity(pa, pa, w.pairs, om, want_match=True, tune=t1)
     assert float((r0.scores - r1.scores).abs().max()) <= 2 * ATOL_S
+
+
+@pytest.mark.parametrize("tune", [183, 228])
+def test_deferred_steps_fall_back_without_room(wl, tune):
+    """A deferred-steps tune whose workspace has no room for the ranked lists
+    (sized as for another tune) matches every pair in the forward instead:
+    the same matchings and scores."""
+    w, pa, om, ref = wl
+    pairs = np.ascontiguousarray(w.pairs, np.int32)
+    small = api.ws_size(pa, pa, pairs, B.params(0.8, 40, tune=18))
+    assert small < api.ws_size(pa, pa, pairs, B.params(0.8, 40, tune=tune))
+    r_def = api.similarity(pa, pa, w.pairs, om, 0.8, 40, want_match=True, tune=tune)
+    r_in = api.similarity(pa, pa, w.pairs, om, 0.8, 40, want_match=True, tune=tune, ws_bytes=small)
+    assert np.array_equal(r_def.match.cpu().numpy(), r_in.match.cpu().numpy())
+    assert np.array_equal(r_def.scores.cpu().numpy(), r_in.scores.cpu().numpy())
+
+
+def test_deferred_steps_in_captured_graph(wl):
+    """The plan and the forward with deferred steps (three kernels) captured
+    once and replayed: the same results as the direct call, bit for bit."""
+    w, pa, om, ref = wl
+    pairs = np.ascontiguousarray(w.pairs, np.int32)
+    tune = 183
+    d_pairs = torch.from_numpy(pairs).to(DEV)
+    ws = api.Workspace(torch.device(DEV))
+    nb = api.ws_size(pa, pa, pairs, B.params(0.8, 40, tune=tune))
+    x_off, m_off = api.out_offsets(pa, pa, pairs)
+    out = {"scores": torch.empty(len(pairs), device=DEV),
+           "match": torch.empty(int(m_off[-1]), dtype=torch.int32, device=DEV)}
+
+    def sim(flags):
+        api.similarity(pa, pa, pairs, om, 0.8, 40, want_match=True, ws=ws, d_pairs=d_pairs, out=out,
+                       check_status=False, flags=flags, ws_bytes=nb, tune=tune)
+
+    sim(0)
+    torch.cuda.synchronize()
+    s0, m0 = out["scores"].clone(), out["match"].clone()
+    g_plan, g_fwd = api.Graph(torch.device(DEV)), api.Graph(torch.device(DEV))
+    with g_plan.capture():
+        sim(B.CF_FLAG_PLAN_ONLY)
+    with g_fwd.capture():
+        sim(B.CF_FLAG_REUSE_PLAN)
+    for _ in range(3):
+        out["scores"].zero_()
+        out["match"].fill_(-7)
+        g_plan.launch()
+        g_fwd.launch()
+        torch.cuda.synchronize()
+        assert torch.equal(out["scores"], s0) and torch.equal(out["match"], m0)
