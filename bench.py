@@ -59,11 +59,21 @@ UNITS = {"ward": "linkages/s"}
 WORKLOAD = WORKLOADS["cfg2"]
 
 
+# --pairs: the large-CFG workload cut to its first N pairs (a smaller case of
+# the same kernel, for an ncu capture that ends in minutes); 0 = all.
+PAIR_LIMIT = 0
+
+
 def workload(name="cfg2"):
+    import dataclasses
+
     from gen import config2, config3, config4, config5
 
-    return {"cfg2": config2, "cfg3": config3, "cfg4": config4, "cfg5": config5, "dist": config2,
-            "optimal": config2, "ward": config2}[name]()
+    w = {"cfg2": config2, "cfg3": config3, "cfg4": config4, "cfg5": config5, "dist": config2,
+         "optimal": config2, "ward": config2}[name]()
+    if name == "cfg3" and PAIR_LIMIT:
+        w = dataclasses.replace(w, pairs=w.pairs[:PAIR_LIMIT])
+    return w
 
 
 def algorithmic(w, K):
@@ -976,9 +986,12 @@ def main():
                     help="kernel configuration id for the forward (0: the autotuner's pick)")
     ap.add_argument("--tune-cache", default=os.environ.get("CF_AUTOTUNE_CACHE") or
                     os.path.join(tempfile.gettempdir(), "cfsim_autotune.cache"))
+    ap.add_argument("--pairs", type=int, default=0,
+                    help="--workload cfg3: only the first N pairs (a smaller case for profiling)")
     args = ap.parse_args()
-    global FIXED_TUNE
+    global FIXED_TUNE, PAIR_LIMIT
     FIXED_TUNE = args.tune
+    PAIR_LIMIT = args.pairs if args.workload == "cfg3" else 0
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
