@@ -199,3 +199,37 @@ def test_graph_and_probe_argument_checks(L):
     n = C.c_size_t(0)
     assert L.cf_probe_ws_size(7, C.byref(n)) == 1
     assert L.cf_probe(0, None, 0, 1, None, C.byref(r)) == 1
+
+
+def test_tune_table_and_deferred_steps_room(L):
+    """The tune table (host only): 240 distinct configurations, ids 181-240 the
+    ones whose matching steps are deferred, and only those tunes size the
+    workspace with room for every pair's ranked lists (6 bytes per entry,
+    plus the list of deferred pairs)."""
+    from paper_1707_02423_gb300 import api
+
+    assert L.cf_num_tunes() == 240
+    seen = set()
+    for t in range(1, 241):
+        d = api.tune_info(t)
+        assert (d["matching"] == "ranked, sequential steps in a second kernel") == (t >= 181)
+        seen.add((d["threads_per_cta"], d["smallest_group"], d["matching"], d["cluster"]))
+    assert len(seen) == 240
+    w = config2(12)
+    buf = build_host(L, w.cfgs_a, 13)
+    pairs = np.ascontiguousarray(w.pairs, np.int32)
+    xs, ms = C.c_int64(0), C.c_int64(0)
+    B.check(L.cf_out_sizes(buf.ctypes.data, buf.ctypes.data, pairs.ctypes.data, len(pairs), C.byref(xs), C.byref(ms)))
+
+    def ws(tune, flags=0):
+        n = C.c_size_t(0)
+        B.check(L.cf_similarity_ws_size(buf.ctypes.data, buf.ctypes.data, pairs.ctypes.data, len(pairs),
+                                        C.byref(B.params(tune=tune, flags=flags)), C.byref(n)))
+        return n.value
+
+    base = ws(18)
+    assert ws(0) == base and ws(180) == base
+    for t in (181, 198, 228, 240):
+        assert ws(t) - base >= 6 * xs.value + 4 * len(pairs)
+    # the plain per-pair form runs the steps in place: no extra room
+    assert ws(228, B.CF_FLAG_PER_PAIR_LAUNCH) == ws(18, B.CF_FLAG_PER_PAIR_LAUNCH)
