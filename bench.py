@@ -272,18 +272,29 @@ def measured_peaks():
         return {}
 
 
-def profiled_traffic(kernel_src: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    with the current kernel source (sha256 of forward.cu); else None."""
+# The sources the forward kernels are built from; a committed profile counts
+# only while their hash is the one it was taken with.
+KERNEL_SOURCES = ("forward.cu", "iterate.cuh", "layout.h", "device_common.cuh")
+
+
+def kernel_sources_sha256(csrc: str) -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()
+
+
+def profiled_traffic(csrc: str):
+    """DRAM bytes per launch of the forward kernel from the committed ncu
+    summary, if it was taken with the current kernel sources; else None."""
     path = os.path.join(ROOT, "profiles", "fwd_batched_kernel_cfg2.md")
     try:
         txt = open(path).read()
     except OSError:
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", txt)
-    h = re.search(r"forward_cu_sha256:\s*([0-9a-f]{64})", txt)
-    cur = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
-    if m and h and h.group(1) == cur:
+    h = re.search(r"kernel_sources_sha256:\s*([0-9a-f]{64})", txt)
+    if m and h and h.group(1) == kernel_sources_sha256(csrc):
         return int(m.group(1))
     return None
 
@@ -903,7 +914,7 @@ def run_ours(args):
     achieved = onchip / fwd_mean_s / 1e9
     peaks = measured_peaks()
     hbm_bytes = int(pack.host.size + pairs_np.nbytes + P * 4 + m_elems * 4)
-    traffic = profiled_traffic(os.path.join(ROOT, "paper_1707_02423_gb300", "csrc", "forward.cu"))
+    traffic = profiled_traffic(os.path.join(ROOT, "paper_1707_02423_gb300", "csrc"))
     cpu_baseline = None  # the oracle is timed at N = 1 only
     if world == 1:
         cpu_v, cpu_n, cpu_dt, cpu_cores, cpu_desc = cpu_oracle(w, args.cpu_seconds)
