@@ -173,7 +173,9 @@ cf_status cf_out_sizes(const void* h_pack_a, const void* h_pack_b, const int32_t
 
 /* Workspace bytes cf_similarity / cf_match need for this pair list.  Uses host
  * copies of the packs and pairs only to size; the device calls take device
- * copies.  A larger workspace is fine. */
+ * copies.  A larger workspace is fine.  params->tune matters: the tunes whose
+ * matching steps are deferred (cf_tune_info.matching 3) need 6 more bytes per
+ * X entry, which this adds; size with the tune the call will use. */
 cf_status cf_similarity_ws_size(const void* h_pack_a, const void* h_pack_b, const int32_t* h_pairs, int32_t P,
                                 const cf_params* params, size_t* bytes);
 
@@ -330,7 +332,11 @@ cf_status cf_similarity_noalloc(const void* d_pack_a, const void* d_pack_b, cons
  * given (a warp, an eighth, quarter or half CTA, or the whole CTA), the matching
  * policy of shared-memory-resident pairs (ranked lists wherever their state
  * fits, only in groups of at most a quarter CTA, or never: rounds of
- * rescans), and the cluster
+ * rescans; or, ids 181-240, ranked lists wherever they fit with the greedy's
+ * sequential steps run by a second kernel, one warp per pair, on lists the
+ * forward leaves in the workspace: 6 bytes per X entry of every pair, which
+ * cf_similarity_ws_size adds for these ids; a workspace without that room
+ * makes the forward run the steps itself), and the cluster
  * tier: pairs too large for one CTA split by rows over the 2, 4 or 8 CTAs of
  * a thread-block cluster with the iterates in distributed shared memory (or,
  * with no cluster tier, iterated by one CTA out of L2).  Every tune gives the
@@ -340,7 +346,9 @@ typedef struct cf_tune_info {
   int32_t threads_per_cta; /* 1024, 768 or 512                                */
   int32_t smallest_group;  /* threads: 32, or threads_per_cta / 8, / 4, / 2, / 1 */
   int32_t matching;        /* 0 ranked where it fits, 1 ranked in groups of at
-                              most a quarter CTA, 2 rescans only                */
+                              most a quarter CTA, 2 rescans only, 3 ranked where
+                              it fits with the steps deferred to a second
+                              kernel                                            */
   int32_t cluster;         /* CTAs per thread-block cluster of the cluster tier
                               (0: none; pairs too large for one CTA then use the
                               global-memory tier)                               */
