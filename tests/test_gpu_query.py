@@ -2,7 +2,8 @@
 corpus pair, top-k per query, the winners' pair list built on the device
 (cf_topk_pairs), and the winners' matchings and scores -- checked against the
 FP64 oracle on a reduced corpus (3 queries x 60 corpus CFGs of the query
-workload's distribution, n 5-400, F = 25, top-4)."""
+workload's distribution, n 5-400, F = 25, top-4), under the default kernel
+configuration and one that defers the greedy's steps to a second kernel."""
 import numpy as np
 import pytest
 
@@ -28,7 +29,8 @@ def _built():
     build.build()
 
 
-def test_query_graph_end_to_end():
+@pytest.mark.parametrize("tune", [0, 183])  # 183: the greedy's steps in a second kernel
+def test_query_graph_end_to_end(tune):
     nq, nc, k = 3, 60, 4
     w = config5(nq, nc)
     pa = api.Pack(w.cfgs_a, w.F, device=DEV)
@@ -37,7 +39,7 @@ def test_query_graph_end_to_end():
     pairs = np.ascontiguousarray(w.pairs, np.int32)
     P = len(pairs)
     d_pairs = torch.from_numpy(pairs).to(DEV)
-    prm = B.params(ALPHA, K)
+    prm = B.params(ALPHA, K, tune=tune)
     ws, mws = api.Workspace(DEV), api.Workspace(DEV)
     ws_bytes = api.ws_size(pa, pb, pairs, prm)
     mws_bytes = api.ws_size_any(pa, pb, nq * k, prm)
@@ -51,11 +53,11 @@ def test_query_graph_end_to_end():
 
     def body():
         api.similarity(pa, pb, pairs, omega, ALPHA, K, ws=ws, d_pairs=d_pairs, out={"scores": scores},
-                       check_status=False, ws_bytes=ws_bytes)
+                       check_status=False, ws_bytes=ws_bytes, tune=tune)
         api.topk(scores.view(nq, nc), k, out=(top, idx))
         api.topk_pairs(idx, out=win)
         api.similarity_dev(pa, pb, win, omega, ALPHA, K, scores=win_scores, match=win_match, ws=mws,
-                           ws_bytes=mws_bytes)
+                           ws_bytes=mws_bytes, tune=tune)
 
     body()
     torch.cuda.synchronize()
